@@ -1,0 +1,334 @@
+"""Throughput of the fused D3Q27 MRT pipe step on one GB300 (JSON line on stdout).
+
+Workload (default): the R = 48 turbulent pipe, 100 x 100 x 480 cells, FP32 shifted
+populations, Re_tau = 181.3 parameters, log-law start with 5 % Gaussian noise, the
+four-mode trigger force active, FP64 statistics every 100 steps and the 16-section
+azimuthal mode analysis every 100 steps.  One bench step = 100 lattice steps (one of
+them with the fused statistics accumulation) + one mode analysis, i.e. every row
+of the hot path.  The population array (518 MB) is larger than L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c2|c3] [--precision f32|f16s|bf16|f64]
+
+Under torchrun (N > 1) every rank runs its own replica of the pipe on its own GPU
+(the path has no exchange step); rank 0 prints the aggregate.
+`--impl reference` times the FP64 oracle on the host cores instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2405_12082_gb300 import workloads as Wk  # noqa: E402
+
+METRIC = "MLUPS (fluid-cell lattice updates per second) of the D3Q27 MRT pipe step"
+BYTES_PER_UPDATE = {"f64": 432, "f32": 216, "f16s": 108, "bf16": 108}
+LBM_STEPS_PER_STEP = 100
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="c2", choices=["c2", "c3"])
+    p.add_argument("--precision", default="f32", choices=["f32", "f16s", "bf16", "f64"])
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload(name):
+    return dict(Wk.C2 if name == "c2" else Wk.C3)
+
+
+def config_json(cfg, args, n_gpus):
+    return {"workload": cfg["name"], "grid": [cfg["nx"], cfg["ny"], cfg["nz"]], "R": cfg["R"],
+            "precision": args.precision, "wall": "halfway", "lbm_steps_per_step": LBM_STEPS_PER_STEP,
+            "stats_every": cfg["stats_every"], "mode_sections": cfg["n_sections"], "n_theta": cfg["n_theta"],
+            "trigger_modes": [m[0] for m in cfg["trigger_modes"]],
+            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas x%d" % n_gpus}
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline): a bounded z-slab sample of the same pipe
+# ---------------------------------------------------------------------------------------
+def _oracle_sample(cfg, nz_sample, min_seconds, max_steps, out_q=None):
+    from oracle import lbm as O
+    tr = O.Trigger(h=cfg["h"], R=cfg["R"], L=cfg["nz"], period=cfg["period"], modes=cfg["trigger_modes"],
+                   t_end=cfg["t_trigger"])
+    run = O.Run(cfg["nx"], cfg["ny"], nz_sample, omega=cfg["omega"], R=cfg["R"], wall="halfway",
+                g=(0.0, 0.0, cfg["h"]), trigger=tr)
+    run.init("loglaw", cfg["noise"], Wk.SEED)
+    n_fluid = int(run.fluid.sum())
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < max_steps:
+        run.step(1)
+        steps += 1
+        if min_seconds > 0 and steps >= 2 and time.perf_counter() - t0 >= min_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"updates": n_fluid * steps, "seconds": dt, "steps": steps, "n_fluid": n_fluid}
+
+
+def oracle_in_child(cfg_name, nz_sample, min_seconds, max_steps):
+    """Runs the oracle sample in a fresh single-threaded interpreter (no GPU context)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench._oracle_sample(bench.workload(%r), %d, %f, %d)))"
+            % (ROOT, cfg_name, nz_sample, min_seconds, max_steps))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(args, cfg):
+    nz_sample = 48
+    res = oracle_in_child(args.workload, nz_sample, 10.0, 40)
+    val = res["updates"] / res["seconds"] / 1e6
+    return {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "FP64 numpy oracle, %d steps of a %dx%dx%d z-slab of the same pipe (%d fluid cells), "
+                      "one thread" % (res["steps"], cfg["nx"], cfg["ny"], nz_sample, res["n_fluid"])}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg = workload(args.workload)
+    nz_sample = 16
+    for _ in range(args.warmup):
+        oracle_in_child(args.workload, nz_sample, 0.0, 1)
+    res = oracle_in_child(args.workload, nz_sample, 0.0, max(args.steps, 1))
+    val = res["updates"] / res["seconds"] / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * res["seconds"] / res["steps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_json(cfg, args, 1),
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "%d oracle steps of a %dx%dx%d z-slab per run" % (
+                                 res["steps"], cfg["nx"], cfg["ny"], nz_sample)},
+            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(precision, workload_name):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "k_step_%s_%s_traffic.txt" % (precision, workload_name))
+    try:
+        with open(path) as fh:
+            for line in fh:
+                if line.startswith("traffic_bytes_per_launch"):
+                    return float(line.split(":")[1])
+    except Exception:
+        return None
+    return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    cfg = workload(args.workload)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, cfg)     # host-only child process, before heavy GPU use
+
+    from paper_2405_12082_gb300 import lbm
+    stream = torch.cuda.current_stream()
+    grid = lbm.make_grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["R"], precision=args.precision, wall="halfway")
+    trig = Wk.trigger_dict(h=cfg["h"], R=cfg["R"], nz=cfg["nz"], period=cfg["period"],
+                           modes=cfg["trigger_modes"], t_end=cfg["t_trigger"])
+    force = lbm.make_force(g=(0.0, 0.0, cfg["h"]), trigger=trig)
+    L = lbm.Lattice(grid, lbm.lbm_relax(cfg["omega"]), force, stream=stream.cuda_stream)
+    L.init("loglaw", noise_amp=cfg["noise"], seed=Wk.SEED + rank)
+    lbm.lbm_stats_enable(L.ctx, cfg["stats_every"])
+    info = L.info()
+    n_fluid = info["n_fluid"]
+    mcfg = lbm.make_modes_cfg(cfg["n_sections"], cfg["r_over_R"], cfg["n_theta"], cfg["n_modes"])
+    E = torch.empty((cfg["n_sections"], len(cfg["r_over_R"]), cfg["n_modes"] + 1), dtype=torch.float64,
+                    device="cuda")
+
+    def one_step():
+        lbm.lbm_step(L.ctx, LBM_STEPS_PER_STEP)
+        lbm.lbm_modes(L.ctx, mcfg, E)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    time.sleep(0.3)
+    lbm.lbm_profile_enable(L.ctx, True)
+    lbm.lbm_profile_read(L.ctx)
+    launches0 = L.info()["launches"]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kernel_ms, kernel_launches = lbm.lbm_profile_read(L.ctx)
+    lbm.lbm_profile_enable(L.ctx, False)
+    launches = L.info()["launches"] - launches0
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    updates = n_fluid * LBM_STEPS_PER_STEP * args.steps * world
+    value = updates / (ms * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: upload the state from pinned host
+    # memory, advance one bench step, read the mode energies and the velocity field back
+    nbytes = info["population_bytes"]
+    host_state = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    lbm.lbm_get_raw(L.ctx, host_state, nbytes)
+    cells = info["n_cells"]
+    dt_np = np.float64 if args.precision == "f64" else np.float32
+    rho_h = torch.empty(cells, dtype=torch.float64 if args.precision == "f64" else torch.float32,
+                        pin_memory=True)
+    u_h = torch.empty(3 * cells, dtype=rho_h.dtype, pin_memory=True)
+    E_h = np.empty((cfg["n_sections"], len(cfg["r_over_R"]), cfg["n_modes"] + 1))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        lbm.lbm_set_raw(L.ctx, host_state, nbytes)
+        lbm.lbm_step(L.ctx, LBM_STEPS_PER_STEP)
+        lbm.lbm_modes(L.ctx, mcfg, E_h)
+        lbm.lbm_moments(L.ctx, rho_h, u_h)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = n_fluid * LBM_STEPS_PER_STEP * args.e2e_steps * world / e2e_s / 1e6
+    d2h = E_h.nbytes + rho_h.numel() * rho_h.element_size() + u_h.numel() * u_h.element_size()
+
+    # health of the run: finite populations after everything above
+    red = lbm.lbm_reduce(L.ctx)
+    L.close()
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = measured_peak()
+    avg_kernel_s = (kernel_ms / kernel_launches) * 1e-3 if kernel_launches else None
+    bpu = BYTES_PER_UPDATE[args.precision]
+    achieved = bpu * n_fluid / avg_kernel_s / 1e9 if avg_kernel_s else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "f32",
+        "storage": args.precision, "data": "synthetic (seeded log-law + noise, paper-shaped pipe)",
+        "config": config_json(cfg, args, world),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": profiled_traffic(args.precision, args.workload),
+                     "kernel": "k_step", "bytes_per_update": bpu, "peak_kind": peak_kind,
+                     "avg_kernel_us": avg_kernel_s * 1e6 if avg_kernel_s else None},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "n_fluid_cells": n_fluid,
+        "nonfinite_cells": red[4],
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

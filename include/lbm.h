@@ -1,0 +1,276 @@
+/*
+ * lbm.h -- C ABI of the GB300 D3Q27 MRT pipe-flow lattice Boltzmann library.
+ *
+ * Method: Magacho, Moriconi and Loureiro, "Persistence of large scale coherent
+ * structures in a turbulent pipe flow through an improved lattice Boltzmann
+ * approach" (arXiv 2405.12082).  One time step is the collision of Eq. (collision)
+ * with the MRT operator of Eqs. (mrt), (lambda), (m*) and the sixth-order Hermite
+ * equilibrium of Eq. (BoltzmannEquilibriumDistribution), the Guo forcing moments
+ * of Eq. (Rmrti), and the streaming of Eq. (streaming), with bounce-back at the
+ * pipe wall (Eqs. (fbc1)-(fbc2)) and periodic streamwise boundaries (Sec. II.B).
+ *
+ * Conventions used by every call below.
+ *   Grid layout.   A field over one pipe is stored [comp][nz][ny][nx] (x fastest);
+ *                  a cell (x, y, z) has flat index (z * ny + y) * nx + x.
+ *   Populations.   Exchanged unshifted, in the paper's velocity order (Appendix A),
+ *                  as double [27][nz][ny][nx].  On the device they are stored
+ *                  shifted by the rest weights, f_i - w_i, in the chosen precision.
+ *   Acceleration.  The body force F of Eq. (macroscopic_u) is taken as an
+ *                  acceleration g: u = sum_i c_i f_i / rho + g / 2.
+ *   Pointers.      Caller buffers may be host or device memory; the library asks
+ *                  the CUDA runtime which.  A call that writes into host memory
+ *                  synchronises the context's stream before returning; a call that
+ *                  only touches device memory is asynchronous on that stream.
+ *                  The caller keeps ownership of every buffer it passes.
+ *   Errors.        Every call except lbm_free returns LBM_OK (0) or a negative
+ *                  status below; lbm_last_error gives the reason.  No call aborts,
+ *                  traps or waits without bound.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------ */
+#define LBM_OK            0
+#define LBM_EINVAL       -1   /* an argument is out of range or inconsistent       */
+#define LBM_ENOMEM       -2   /* a device or host allocation failed                */
+#define LBM_ECUDA        -3   /* a CUDA runtime call or a kernel launch failed     */
+#define LBM_EUNSTABLE    -4   /* non-finite populations or mass drift detected     */
+#define LBM_ETIMEOUT     -5   /* a bounded device-side wait expired                */
+#define LBM_EUNSUPPORTED -6   /* valid request this build or state cannot serve    */
+
+/* ---- storage precision of the populations (collision runs in FP32 for all but F64) */
+#define LBM_F64   0   /* double storage, double collision                            */
+#define LBM_F32   1   /* float storage of f - w, float collision                     */
+#define LBM_F16S  2   /* IEEE half of (f - w) * 2^s, float collision                 */
+#define LBM_BF16  3   /* bfloat16 of f - w, float collision                          */
+
+/* ---- geometry ------------------------------------------------------------------- */
+#define LBM_PIPE  0   /* circular pipe along z, axis at ((nx-1)/2, (ny-1)/2); a cell is
+                         fluid iff its distance to the axis is < R; periodic in z       */
+#define LBM_BOX   1   /* fully periodic box, every cell fluid (R unused)              */
+
+/* ---- wall treatment (Sec. II.A) ------------------------------------------------- */
+#define LBM_HALFWAY 0 /* half-way bounce-back: Eqs. (fbc1)-(fbc2) at Delta = 1/2      */
+#define LBM_FULLWAY 1 /* full-way bounce-back: solid cells reverse their populations  */
+#define LBM_BOUZIDI 2 /* Eqs. (fbc1)-(fbc2) with the exact wall distance Delta        */
+
+/* ---- initial velocity profiles ---------------------------------------------------- */
+#define LBM_REST    0 /* u = 0                                                         */
+#define LBM_LAMINAR 1 /* Hagen-Poiseuille u_z = g_z (R^2 - r^2) / (4 nu)              */
+#define LBM_LOGLAW  2 /* Sec. II.B mean profile U+ = delta+ (delta+ <= 10.8), else
+                         ln(delta+) / 0.4 + 5, with u* = sqrt(g_z R / 2)               */
+
+/* ---- objectives of the adjoint ---------------------------------------------------- */
+#define LBM_J_UBULK 0 /* J = (1/T) sum_t (1/N_fluid) sum_x u_z(x, t)                  */
+#define LBM_J_WSS   1 /* J = (1/T) sum_t tau_w(t), axial momentum exchanged with the
+                         wall per step divided by the wall area 2 pi R nz              */
+
+#define LBM_MAX_TRIGGER_MODES 8
+#define LBM_MAX_MEMBERS       64
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Grid of one pipe.  nx, ny, nz >= 1 (a pipe also needs nx, ny >= 3).  A pipe must
+ * leave at least one solid cell between the fluid and the box edge in x and y.
+ * f16_log2_scale: exponent s of the LBM_F16S scale 2^s (0 selects 16; 1..24 valid). */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t geometry;       /* LBM_PIPE | LBM_BOX                                   */
+    double  R;              /* pipe radius in lattice units (LBM_PIPE)               */
+    int32_t precision;      /* LBM_F64 | LBM_F32 | LBM_F16S | LBM_BF16               */
+    int32_t wall;           /* LBM_HALFWAY | LBM_FULLWAY | LBM_BOUZIDI               */
+    int32_t f16_log2_scale;
+} lbm_grid;
+
+/* Relaxation matrix of Eq. (lambda): Lambda = diag[1,1,1,1, omega x5, 1 x18], with
+ * omega = 1/tau = (nu / c_s^2 + 1/2)^{-1}.  0 < omega < 2. */
+typedef struct {
+    double omega;
+} lbm_relax;
+
+/* Acceleration g(x, t) acting on every fluid cell (Sec. II.B):
+ *   g = (g[0], g[1], g[2])                                   constant part (h along z)
+ *     + trigger force of Eq. (TurbForce), while trigger != 0 and t < t_end
+ *     + (0, 0, gz_field[cell])                               if gz_field != NULL
+ * The trigger is a sum over n_modes azimuthal modes; mode q has wavenumber
+ * k_theta[q] >= 1, amplitude A0 * weight[q] and enters as cos(k_theta theta +
+ * phase[q]) and sin(k_theta theta + phase[q]).  The paper's force is n_modes = 1,
+ * k_theta = 2, weight = 1, phase = 0, kz = 3, A0 = 50, kappa = 0.5, l0 = 0.2 R,
+ * l = 0.4 R, period = 0.052 T_LET, h = g[2].  theta = atan2(y - y_c, x - x_c), the
+ * streamwise coordinate is the cell index z and L = nz.  The force is applied in
+ * the band R - l0 - l <= r <= R - l0.
+ * gz_field: device pointer, [nz][ny][nx] of double for LBM_F64 and of float for
+ * the other precisions; caller-owned, must stay valid while steps run. */
+typedef struct {
+    double  g[3];
+    int32_t trigger;
+    int32_t n_modes;
+    int32_t k_theta[LBM_MAX_TRIGGER_MODES];
+    double  weight[LBM_MAX_TRIGGER_MODES];
+    double  phase[LBM_MAX_TRIGGER_MODES];
+    double  A0, kappa, l0, l, period, h;
+    int32_t kz;
+    int64_t t_end;
+    const void *gz_field;
+} lbm_force;
+
+/* Cross-section ring analysis of Sec. II.C (see lbm_modes). */
+typedef struct {
+    int32_t n_sections;     /* sections at z_s = floor(s nz / n_sections), >= 1      */
+    int32_t n_rings;        /* 1..16 rings                                           */
+    double  r_over_R[16];   /* ring radius / R; the paper uses 0.78                  */
+    int32_t n_theta;        /* samples per ring, 8..4096                             */
+    int32_t n_modes;        /* highest mode M reported, 0 <= M < n_theta             */
+} lbm_modes_cfg;
+
+typedef struct {
+    int64_t n_cells;        /* nx * ny * nz of the selected member                   */
+    int64_t n_fluid;        /* fluid cells of the selected member                    */
+    int64_t t;              /* completed time steps                                  */
+    int64_t population_bytes; /* device bytes of the population array (all members)*/
+    int32_t n_members;
+    int32_t precision;
+    int64_t launches;       /* kernels this context has launched so far              */
+} lbm_info;
+
+/* ==== life cycle ====================================================================== */
+
+/* Creates a context holding one pipe: allocates its populations on the device
+ * (owned by the library, freed by lbm_free) and sets them to rest, f = w, t = 0.
+ * stream: a cudaStream_t (NULL = legacy default stream) on which every later call
+ * of this context runs.  Errors: LBM_EINVAL (bad grid, omega, force),
+ * LBM_ENOMEM, LBM_ECUDA.  *out is NULL on error. */
+int lbm_create(lbm_ctx **out, const lbm_grid *grid, const lbm_relax *relax,
+               const lbm_force *force, void *stream);
+
+/* An ensemble of n independent pipes (1 <= n <= LBM_MAX_MEMBERS) advanced together
+ * by one kernel launch per time step.  grids[k], relax[k], force[k] describe member
+ * k; all members share precision and wall.  Per-member calls act on the member
+ * chosen by lbm_select_member (default 0). */
+int lbm_ensemble_create(lbm_ctx **out, int32_t n, const lbm_grid *grids,
+                        const lbm_relax *relax, const lbm_force *force, void *stream);
+
+/* Releases everything the context owns.  NULL-safe.  Synchronises its stream. */
+void lbm_free(lbm_ctx *ctx);
+
+/* Text of the last error of ctx (or of the calling thread's last failed
+ * lbm_create / lbm_ensemble_create if ctx is NULL).  Never NULL. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+int lbm_set_stream(lbm_ctx *ctx, void *stream);
+int lbm_select_member(lbm_ctx *ctx, int32_t member);
+int lbm_get_info(lbm_ctx *ctx, lbm_info *info);
+
+/* Replace the relaxation or the force of the selected member (Eq. (lambda),
+ * Sec. II.B).  Takes effect for the next step. */
+int lbm_set_relax(lbm_ctx *ctx, const lbm_relax *relax);
+int lbm_set_force(lbm_ctx *ctx, const lbm_force *force);
+
+/* ==== initial state ================================================================== */
+
+/* Every member: f = f^eq(rho = 1, u_0) (Eq. (BoltzmannEquilibriumDistribution)) on
+ * fluid cells, f = w elsewhere; t = 0; statistics cleared.  u_0 is the profile plus
+ * noise_amp times a standard normal per cell and component drawn from SplitMix64
+ * (seed + member index) with Box-Muller: normal number (3 c + k) of cell c, component
+ * k, uses outputs 2(3c+k) and 2(3c+k)+1.  Errors: LBM_EINVAL. */
+int lbm_init(lbm_ctx *ctx, int32_t profile, double noise_amp, uint64_t seed);
+
+/* Selected member: f = f^eq(rho, u) on fluid cells from caller fields
+ * rho [nz][ny][nx] and u [3][nz][ny][nx] (double, host or device); t = 0. */
+int lbm_init_fields(lbm_ctx *ctx, const double *rho, const double *u);
+
+/* ==== time stepping ================================================================== */
+
+/* Enqueues n >= 0 time steps of every member (Eqs. (collision), (streaming)):
+ * collision with the MRT operator, forcing, streaming with the wall rule and
+ * periodic z.  Steps whose index t is a multiple of the statistics interval also
+ * accumulate the statistics (lbm_stats_enable).  Asynchronous unless a stability
+ * check is due (lbm_set_check), which synchronises and may return LBM_EUNSTABLE. */
+int lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Every `every` steps (0 = never), lbm_step reduces mass and checks for
+ * non-finite populations; a relative mass drift above max_mass_drift or any
+ * non-finite value returns LBM_EUNSTABLE. */
+int lbm_set_check(lbm_ctx *ctx, int64_t every, double max_mass_drift);
+
+/* ==== observables ==================================================================== */
+
+/* Eqs. (macroscopic_rho), (macroscopic_u) of the selected member at the current t:
+ * rho [nz][ny][nx] and u [3][nz][ny][nx], u = sum c f / rho + g(x, t) / 2.  Element
+ * type double for LBM_F64, float otherwise.  Solid cells get rho = 0, u = 0. */
+int lbm_moments(lbm_ctx *ctx, void *rho, void *u);
+
+/* Populations of the selected member at the current t, unshifted, double
+ * [27][nz][ny][nx].  Solid cells of a half-way or Bouzidi wall read as w. */
+int lbm_get_populations(lbm_ctx *ctx, double *f);
+
+/* Overwrite the populations of the selected member (same layout); solid cells
+ * of a half-way or Bouzidi wall are ignored. */
+int lbm_set_populations(lbm_ctx *ctx, const double *f);
+
+/* The raw device population array of the whole context (population_bytes of
+ * lbm_get_info), in storage precision, in the layout of the current t.  Used to
+ * save and restore a state bit-exactly. */
+int lbm_get_raw(lbm_ctx *ctx, void *buf, size_t bytes);
+int lbm_set_raw(lbm_ctx *ctx, const void *buf, size_t bytes);
+
+/* Sum over fluid cells of the selected member, in FP64: out[0] = sum (rho - 1),
+ * out[1..3] = sum of momentum sum_i c_i f_i, out[4] = number of cells with a
+ * non-finite population.  out is host memory; the call synchronises. */
+int lbm_reduce(lbm_ctx *ctx, double *out);
+
+/* Point statistics of Sec. III.B: from now on, every step t with t % every == 0
+ * adds u_z^k (k = 1..4) of every fluid cell of every member to FP64 accumulators
+ * (u_z before the collision of step t, as lbm_moments reports it).  every >= 1;
+ * resets the accumulators. */
+int lbm_stats_enable(lbm_ctx *ctx, int32_t every);
+
+/* Accumulators of the selected member: acc [4][nz][ny][nx] double (sum of u_z^k),
+ * and the number of samples taken. */
+int lbm_stats_get(lbm_ctx *ctx, double *acc, int64_t *count);
+
+/* Coherent-structure analysis of Sec. II.C for the selected member at the
+ * current t: for every section s and ring j, u_z is sampled bilinearly at
+ * theta_n = 2 pi n / n_theta on the circle of radius r_over_R[j] R and
+ * E[s][j][m] = |sum_n u_z(theta_n) exp(-i m theta_n)|^2 / n_theta^2, m = 0..n_modes,
+ * in double.  For m >= 1 E_m is proportional to the Fourier power of the
+ * correlation R_uu of Eq. (newcorrelation) at Delta r = 0 (Wiener-Khinchin); the
+ * dominant mode is its argmax over 1 <= m <= 10. */
+int lbm_modes(lbm_ctx *ctx, const lbm_modes_cfg *cfg, double *E);
+
+/* ==== adjoint ======================================================================== */
+
+/* Runs T >= 1 forward steps of the selected single-pipe context from its current
+ * state and returns J (objective LBM_J_UBULK or LBM_J_WSS) together with its
+ * gradient with respect to the per-cell axial acceleration, dJ_dgz [nz][ny][nx]
+ * (double, host or device), and to the shear rate omega (*dJ_domega).  The
+ * reverse sweep recomputes the forward from checkpoints taken every
+ * `checkpoint_every` steps (0 = about sqrt(T)).  On return the context holds the
+ * state after the T steps.  Needs a context with LBM_HALFWAY wall and LBM_F32 or
+ * LBM_F64 precision and no trigger (LBM_EUNSUPPORTED otherwise). */
+int lbm_adjoint(lbm_ctx *ctx, int64_t T, int32_t objective, int64_t checkpoint_every,
+                double *J, double *dJ_dgz, double *dJ_domega);
+
+/* ==== timing =========================================================================== */
+
+/* While enabled, every step-kernel launch is bracketed by CUDA events on the
+ * context's stream; lbm_profile_read returns the summed device time (ms) and the
+ * number of timed launches, then clears them.  lbm_profile_read synchronises. */
+int lbm_profile_enable(lbm_ctx *ctx, int32_t on);
+int lbm_profile_read(lbm_ctx *ctx, double *ms, int64_t *launches);
+
+/* Fills the pipe's per-column fluid mask mask[ny][nx] (1 fluid, 0 solid) of the
+ * selected member, exactly as the kernels decide it.  Host memory. */
+int lbm_fluid_mask(lbm_ctx *ctx, uint8_t *mask);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,721 @@
+// lbm_api.cu -- the C ABI of include/lbm.h: contexts, validation, memory, launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using lbm::Member;
+using lbm::StepArgs;
+
+struct lbm_ctx {
+    int precision = LBM_F32;
+    int wall = LBM_HALFWAY;
+    cudaStream_t stream = nullptr;
+    std::vector<Member> hm;          // host copies of the member descriptors
+    std::vector<lbm_grid> grids;
+    std::vector<lbm_force> forces;
+    Member *dm = nullptr;            // device copies
+    int sel = 0;
+    void *pops = nullptr;
+    int64_t stride = 0;              // cells per population plane
+    size_t esize = 0;                // bytes per stored population
+    int32_t nblocks = 0;
+    int64_t t = 0;
+    float f16_scale = 1.f, f16_inv = 1.f;
+    double *stats = nullptr;
+    int32_t stats_every = 0;
+    int64_t stats_count = 0;
+    void *scratch = nullptr;         // staging for host buffers
+    size_t scratch_bytes = 0;
+    double *partials = nullptr;      // reduction partials + final (device)
+    int64_t check_every = 0;
+    double max_drift = 0;
+    std::vector<double> mass0;
+    std::vector<bool> mass0_valid;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int set_err(lbm_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_create_error = buf;
+    return code;
+}
+
+int cuda_err(lbm_ctx *c, cudaError_t e, const char *what) {
+    return set_err(c, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(c, call)                                          \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_err((c), e_, #call);    \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// fluid iff (2x - nx + 1)^2 + (2y - ny + 1)^2 < 4 R^2  <=>  ... <= ceil(4 R^2) - 1
+int64_t d2max_of(double R) { return (int64_t)std::ceil(4.0 * R * R) - 1; }
+
+bool col_fluid_host(const Member &d, int x, int y) {
+    if (d.geometry == LBM_BOX) return true;
+    int64_t X = 2 * (int64_t)x - d.nx + 1, Y = 2 * (int64_t)y - d.ny + 1;
+    return X * X + Y * Y <= d.d2max;
+}
+
+int check_force(lbm_ctx *c, const lbm_force *f) {
+    if (!f) return LBM_OK;
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(f->g[k])) return set_err(c, LBM_EINVAL, "force.g[%d] is not finite", k);
+    if (f->trigger) {
+        if (f->n_modes < 1 || f->n_modes > LBM_MAX_TRIGGER_MODES)
+            return set_err(c, LBM_EINVAL, "force.n_modes must be in 1..%d", LBM_MAX_TRIGGER_MODES);
+        for (int q = 0; q < f->n_modes; ++q)
+            if (f->k_theta[q] < 1 || f->k_theta[q] > 64)
+                return set_err(c, LBM_EINVAL, "force.k_theta[%d] must be in 1..64", q);
+        if (!(f->period > 0)) return set_err(c, LBM_EINVAL, "force.period must be > 0");
+        if (!(f->l > 0)) return set_err(c, LBM_EINVAL, "force.l must be > 0");
+        if (!std::isfinite(f->A0) || !std::isfinite(f->kappa) || !std::isfinite(f->h) || !std::isfinite(f->l0))
+            return set_err(c, LBM_EINVAL, "force trigger parameters must be finite");
+    }
+    return LBM_OK;
+}
+
+void fill_force(Member &d, const lbm_force *f) {
+    for (int k = 0; k < 3; ++k) d.g[k] = f ? f->g[k] : 0.0;
+    d.trig = (f && f->trigger) ? 1 : 0;
+    d.n_modes = d.trig ? f->n_modes : 0;
+    d.kz = f ? f->kz : 0;
+    for (int q = 0; q < LBM_MAX_TRIGGER_MODES; ++q) {
+        const bool on = d.trig && q < d.n_modes;
+        d.k_theta[q] = on ? f->k_theta[q] : 1;
+        d.amp[q] = on ? f->h * f->A0 * f->weight[q] : 0.0;
+        d.cph[q] = on ? std::cos(f->phase[q]) : 1.0;
+        d.sph[q] = on ? std::sin(f->phase[q]) : 0.0;
+    }
+    d.kappa = f ? f->kappa : 0.0;
+    d.l0 = f ? f->l0 : 0.0;
+    d.l = f ? f->l : 1.0;
+    d.period = (f && f->period > 0) ? f->period : 1.0;
+    d.t_end = f ? f->t_end : 0;
+    d.gz_field = f ? f->gz_field : nullptr;
+}
+
+int build_member(lbm_ctx *c, const lbm_grid *g, const lbm_relax *r, const lbm_force *f, Member &d) {
+    if (!g || !r) return set_err(c, LBM_EINVAL, "grid and relax must not be NULL");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return set_err(c, LBM_EINVAL, "grid sizes must be >= 1");
+    const int64_t cells = (int64_t)g->nx * g->ny * g->nz;
+    if (cells >= (1ll << 31)) return set_err(c, LBM_EINVAL, "a member may hold at most 2^31-1 cells");
+    if (g->geometry != LBM_PIPE && g->geometry != LBM_BOX) return set_err(c, LBM_EINVAL, "unknown geometry");
+    if (!(r->omega > 0.0 && r->omega < 2.0)) return set_err(c, LBM_EINVAL, "omega must be in (0, 2)");
+    int rc = check_force(c, f);
+    if (rc) return rc;
+    std::memset(&d, 0, sizeof d);
+    d.nx = g->nx; d.ny = g->ny; d.nz = g->nz; d.geometry = g->geometry;
+    d.cells = cells;
+    d.R = g->R;
+    d.omega = r->omega;
+    if (g->geometry == LBM_PIPE) {
+        if (g->nx < 3 || g->ny < 3) return set_err(c, LBM_EINVAL, "a pipe needs nx, ny >= 3");
+        if (!(g->R > 0.0) || !std::isfinite(g->R)) return set_err(c, LBM_EINVAL, "pipe radius must be > 0");
+        d.d2max = d2max_of(g->R);
+        for (int x = 0; x < g->nx; ++x)
+            if (col_fluid_host(d, x, 0) || col_fluid_host(d, x, g->ny - 1))
+                return set_err(c, LBM_EINVAL, "pipe must leave a solid margin at the box edge (R too large)");
+        for (int y = 0; y < g->ny; ++y)
+            if (col_fluid_host(d, 0, y) || col_fluid_host(d, g->nx - 1, y))
+                return set_err(c, LBM_EINVAL, "pipe must leave a solid margin at the box edge (R too large)");
+    }
+    int64_t ncol = 0;
+    for (int y = 0; y < g->ny; ++y)
+        for (int x = 0; x < g->nx; ++x) ncol += col_fluid_host(d, x, y);
+    d.n_fluid = ncol * g->nz;
+    fill_force(d, f);
+    lbm::fastdiv_setup((uint32_t)g->nx, d.nx_mul, d.nx_shr);
+    lbm::fastdiv_setup((uint32_t)g->ny, d.ny_mul, d.ny_shr);
+    return LBM_OK;
+}
+
+size_t esize_of(int p) {
+    switch (p) {
+        case LBM_F64: return 8;
+        case LBM_F32: return 4;
+        case LBM_F16S: return 2;
+        case LBM_BF16: return 2;
+    }
+    return 0;
+}
+
+StepArgs make_args(const lbm_ctx *c, int64_t t) {
+    StepArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.pops = c->pops;
+    a.stride = c->stride;
+    a.members = c->dm;
+    a.n_members = (int32_t)c->hm.size();
+    a.nblocks_total = c->nblocks;
+    a.t = t;
+    a.f16_scale = c->f16_scale;
+    a.f16_inv = c->f16_inv;
+    a.stats = c->stats;
+    for (size_t m = 0; m < c->hm.size(); ++m) {
+        const Member &d = c->hm[m];
+        a.st[m] = (d.trig && t < d.t_end) ? std::sin(2.0 * M_PI * (double)t / d.period) : 0.0;
+        a.block0[m] = (int32_t)d.block0;
+    }
+    a.block0[c->hm.size()] = c->nblocks;
+    return a;
+}
+
+int upload_members(lbm_ctx *c) {
+    LBM_CUDA(c, cudaMemcpyAsync(c->dm, c->hm.data(), sizeof(Member) * c->hm.size(), cudaMemcpyHostToDevice,
+                                c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int ensure_scratch(lbm_ctx *c, size_t bytes) {
+    if (bytes <= c->scratch_bytes) return LBM_OK;
+    if (c->scratch) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->scratch);
+        c->scratch = nullptr;
+        c->scratch_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->scratch, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, LBM_ENOMEM, "cannot allocate %zu bytes of staging memory", bytes);
+    }
+    c->scratch_bytes = bytes;
+    return LBM_OK;
+}
+
+int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_relax *relax,
+                  const lbm_force *force, void *stream) {
+    if (!out) return set_err(nullptr, LBM_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    if (n < 1 || n > LBM_MAX_MEMBERS) return set_err(nullptr, LBM_EINVAL, "member count must be in 1..%d", LBM_MAX_MEMBERS);
+    if (!grids || !relax) return set_err(nullptr, LBM_EINVAL, "grid and relax must not be NULL");
+    const int prec = grids[0].precision, wall = grids[0].wall;
+    if (esize_of(prec) == 0) return set_err(nullptr, LBM_EINVAL, "unknown precision %d", prec);
+    if (wall != LBM_HALFWAY && wall != LBM_FULLWAY && wall != LBM_BOUZIDI)
+        return set_err(nullptr, LBM_EINVAL, "unknown wall %d", wall);
+    int s16 = grids[0].f16_log2_scale;
+    if (s16 == 0) s16 = 16;
+    if (s16 < 1 || s16 > 24) return set_err(nullptr, LBM_EINVAL, "f16_log2_scale must be in 1..24");
+    lbm_ctx *c = new lbm_ctx();
+    c->precision = prec;
+    c->wall = wall;
+    c->stream = (cudaStream_t)stream;
+    c->f16_scale = std::ldexp(1.0f, s16);
+    c->f16_inv = std::ldexp(1.0f, -s16);
+    c->hm.resize(n);
+    int64_t off = 0, blk = 0;
+    for (int k = 0; k < n; ++k) {
+        if (grids[k].precision != prec || grids[k].wall != wall) {
+            delete c;
+            return set_err(nullptr, LBM_EINVAL, "all members must share precision and wall");
+        }
+        int rc = build_member(nullptr, &grids[k], &relax[k], force ? &force[k] : nullptr, c->hm[k]);
+        if (rc) { delete c; return rc; }
+        c->hm[k].off = off;
+        c->hm[k].block0 = blk;
+        off += ceil_div(c->hm[k].cells, 64) * 64;   // keep every member 64-cell aligned
+        blk += ceil_div(c->hm[k].cells, lbm::STEP_BLOCK_HOST);
+        c->grids.push_back(grids[k]);
+        lbm_force fz;
+        std::memset(&fz, 0, sizeof fz);
+        c->forces.push_back(force ? force[k] : fz);
+    }
+    if (blk >= (1ll << 31)) { delete c; return set_err(nullptr, LBM_EINVAL, "grid too large"); }
+    c->stride = off;
+    c->nblocks = (int32_t)blk;
+    c->esize = esize_of(prec);
+    c->mass0.assign(n, 0.0);
+    c->mass0_valid.assign(n, false);
+    const size_t bytes = (size_t)27 * (size_t)c->stride * c->esize;
+    cudaError_t e = cudaMalloc(&c->pops, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return set_err(nullptr, LBM_ENOMEM, "cannot allocate %zu bytes of populations", bytes);
+    }
+    e = cudaMalloc((void **)&c->dm, sizeof(Member) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->partials, sizeof(double) * (lbm::REDUCE_MAX_BLOCKS * 5 + 8));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        lbm_free(c);
+        return set_err(nullptr, LBM_ENOMEM, "cannot allocate context buffers");
+    }
+    e = cudaMemsetAsync(c->pops, 0, bytes, c->stream);   // f - w = 0: rest state
+    if (e != cudaSuccess) {
+        lbm_free(c);
+        return set_err(nullptr, LBM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+    int rc = upload_members(c);
+    if (rc) {
+        g_create_error = c->err;
+        lbm_free(c);
+        return rc;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+template <class F>
+int dispatch(lbm_ctx *c, F &&f) {
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (c->precision) {
+        case LBM_F64: e = f(std::integral_constant<int, LBM_F64>{}); break;
+        case LBM_F32: e = f(std::integral_constant<int, LBM_F32>{}); break;
+        case LBM_F16S: e = f(std::integral_constant<int, LBM_F16S>{}); break;
+        case LBM_BF16: e = f(std::integral_constant<int, LBM_BF16>{}); break;
+    }
+    if (e != cudaSuccess) return cuda_err(c, e, "kernel launch");
+    c->launches++;
+    return LBM_OK;
+}
+
+int reduce_member(lbm_ctx *c, int m, double *host_out) {
+    const StepArgs a = make_args(c, c->t);
+    double *partials = c->partials, *dout = c->partials + lbm::REDUCE_MAX_BLOCKS * 5;
+    int rc = dispatch(c, [&](auto P) {
+        return lbm::launch_reduce<decltype(P)::value>(c->wall, (int)(c->t & 1), a, c->hm[m], m, partials,
+                                                      lbm::REDUCE_MAX_BLOCKS, dout, c->stream);
+    });
+    if (rc) return rc;
+    c->launches++;   // the final pass
+    LBM_CUDA(c, cudaMemcpyAsync(host_out, dout, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int stability_check(lbm_ctx *c) {
+    for (size_t m = 0; m < c->hm.size(); ++m) {
+        double r[5];
+        int rc = reduce_member(c, (int)m, r);
+        if (rc) return rc;
+        if (r[4] > 0) return set_err(c, LBM_EUNSTABLE, "member %zu: %.0f cells with non-finite populations at t=%lld",
+                                     m, r[4], (long long)c->t);
+        if (!c->mass0_valid[m]) {
+            c->mass0[m] = r[0];
+            c->mass0_valid[m] = true;
+        } else {
+            const double drift = std::fabs(r[0] - c->mass0[m]) / (double)std::max<int64_t>(c->hm[m].n_fluid, 1);
+            if (!(drift <= c->max_drift))
+                return set_err(c, LBM_EUNSTABLE, "member %zu: relative mass drift %.3e above %.3e at t=%lld", m, drift,
+                               c->max_drift, (long long)c->t);
+        }
+    }
+    return LBM_OK;
+}
+
+int event_pair(lbm_ctx *c, cudaEvent_t &a, cudaEvent_t &b) {
+    while (c->ev.size() < c->ev_used + 2) {
+        cudaEvent_t e;
+        LBM_CUDA(c, cudaEventCreate(&e));
+        c->ev.push_back(e);
+    }
+    a = c->ev[c->ev_used];
+    b = c->ev[c->ev_used + 1];
+    c->ev_used += 2;
+    return LBM_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+int lbm_create(lbm_ctx **out, const lbm_grid *grid, const lbm_relax *relax, const lbm_force *force, void *stream) {
+    return create_common(out, 1, grid, relax, force, stream);
+}
+
+int lbm_ensemble_create(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_relax *relax,
+                        const lbm_force *force, void *stream) {
+    return create_common(out, n, grids, relax, force, stream);
+}
+
+void lbm_free(lbm_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->pops);
+    cudaFree(c->dm);
+    cudaFree(c->stats);
+    cudaFree(c->scratch);
+    cudaFree(c->partials);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete c;
+}
+
+const char *lbm_last_error(const lbm_ctx *c) {
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+int lbm_set_stream(lbm_ctx *c, void *stream) {
+    if (!c) return LBM_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+int lbm_select_member(lbm_ctx *c, int32_t m) {
+    if (!c) return LBM_EINVAL;
+    if (m < 0 || m >= (int32_t)c->hm.size()) return set_err(c, LBM_EINVAL, "member %d out of range", m);
+    c->sel = m;
+    return LBM_OK;
+}
+
+int lbm_get_info(lbm_ctx *c, lbm_info *info) {
+    if (!c || !info) return LBM_EINVAL;
+    const Member &d = c->hm[c->sel];
+    info->n_cells = d.cells;
+    info->n_fluid = d.n_fluid;
+    info->t = c->t;
+    info->population_bytes = (int64_t)27 * c->stride * (int64_t)c->esize;
+    info->n_members = (int32_t)c->hm.size();
+    info->precision = c->precision;
+    info->launches = c->launches;
+    return LBM_OK;
+}
+
+int lbm_set_relax(lbm_ctx *c, const lbm_relax *r) {
+    if (!c || !r) return LBM_EINVAL;
+    if (!(r->omega > 0.0 && r->omega < 2.0)) return set_err(c, LBM_EINVAL, "omega must be in (0, 2)");
+    c->hm[c->sel].omega = r->omega;
+    return upload_members(c);
+}
+
+int lbm_set_force(lbm_ctx *c, const lbm_force *f) {
+    if (!c) return LBM_EINVAL;
+    int rc = check_force(c, f);
+    if (rc) return rc;
+    fill_force(c->hm[c->sel], f);
+    lbm_force fz;
+    std::memset(&fz, 0, sizeof fz);
+    c->forces[c->sel] = f ? *f : fz;
+    return upload_members(c);
+}
+
+int lbm_init(lbm_ctx *c, int32_t profile, double noise_amp, uint64_t seed) {
+    if (!c) return LBM_EINVAL;
+    if (profile != LBM_REST && profile != LBM_LAMINAR && profile != LBM_LOGLAW)
+        return set_err(c, LBM_EINVAL, "unknown profile %d", profile);
+    if (!std::isfinite(noise_amp)) return set_err(c, LBM_EINVAL, "noise_amp must be finite");
+    for (size_t m = 0; m < c->hm.size(); ++m) {
+        if (c->hm[m].geometry != LBM_PIPE && profile != LBM_REST)
+            return set_err(c, LBM_EINVAL, "profiles other than REST need a pipe");
+    }
+    c->t = 0;
+    LBM_CUDA(c, cudaMemsetAsync(c->pops, 0, (size_t)27 * c->stride * c->esize, c->stream));
+    const StepArgs a = make_args(c, 0);
+    for (size_t m = 0; m < c->hm.size(); ++m) {
+        int rc = dispatch(c, [&](auto P) {
+            return lbm::launch_init<decltype(P)::value>(c->wall, a, c->hm[m], (int)m, profile, noise_amp,
+                                                        seed + (uint64_t)m, nullptr, nullptr, c->stream);
+        });
+        if (rc) return rc;
+        c->mass0_valid[m] = false;
+    }
+    if (c->stats) {
+        LBM_CUDA(c, cudaMemsetAsync(c->stats, 0, sizeof(double) * 4 * c->stride, c->stream));
+        c->stats_count = 0;
+    }
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_ctx *c, const double *rho, const double *u) {
+    if (!c || !rho || !u) return LBM_EINVAL;
+    const Member &d = c->hm[c->sel];
+    const size_t n = (size_t)d.cells;
+    const double *drho = rho, *du = u;
+    const bool dev = is_device_ptr(rho) && is_device_ptr(u);
+    if (!dev) {
+        int rc = ensure_scratch(c, 4 * n * sizeof(double));
+        if (rc) return rc;
+        double *s = (double *)c->scratch;
+        LBM_CUDA(c, cudaMemcpyAsync(s, rho, n * sizeof(double), cudaMemcpyDefault, c->stream));
+        LBM_CUDA(c, cudaMemcpyAsync(s + n, u, 3 * n * sizeof(double), cudaMemcpyDefault, c->stream));
+        drho = s;
+        du = s + n;
+    }
+    if (c->t & 1) return set_err(c, LBM_EUNSUPPORTED, "lbm_init_fields resets t to 0; call it at even t");
+    c->t = 0;
+    const StepArgs a = make_args(c, 0);
+    const int m = c->sel;
+    int rc = dispatch(c, [&](auto P) {
+        return lbm::launch_init<decltype(P)::value>(c->wall, a, c->hm[m], m, LBM_REST, 0.0, 0, drho, du, c->stream);
+    });
+    if (rc) return rc;
+    c->mass0_valid[m] = false;
+    if (!dev) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_set_check(lbm_ctx *c, int64_t every, double max_mass_drift) {
+    if (!c) return LBM_EINVAL;
+    if (every < 0 || !(max_mass_drift >= 0)) return set_err(c, LBM_EINVAL, "bad check parameters");
+    c->check_every = every;
+    c->max_drift = max_mass_drift;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *c, int64_t n) {
+    if (!c) return LBM_EINVAL;
+    if (n < 0) return set_err(c, LBM_EINVAL, "n must be >= 0");
+    for (int64_t k = 0; k < n; ++k) {
+        const bool stats = c->stats && c->stats_every > 0 && (c->t % c->stats_every == 0);
+        const StepArgs a = make_args(c, c->t);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (c->prof) {
+            int rc = event_pair(c, e0, e1);
+            if (rc) return rc;
+            LBM_CUDA(c, cudaEventRecord(e0, c->stream));
+        }
+        int rc = dispatch(c, [&](auto P) {
+            return lbm::launch_step<decltype(P)::value>(c->wall, (int)(c->t & 1), stats, a, lbm::STEP_BLOCK_HOST,
+                                                        c->stream);
+        });
+        if (rc) return rc;
+        if (c->prof) LBM_CUDA(c, cudaEventRecord(e1, c->stream));
+        c->t++;
+        if (stats) c->stats_count++;
+        if (c->check_every > 0 && c->t % c->check_every == 0) {
+            rc = stability_check(c);
+            if (rc) return rc;
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx *c, void *rho, void *u) {
+    if (!c || !rho || !u) return LBM_EINVAL;
+    const int m = c->sel;
+    const Member &d = c->hm[m];
+    const size_t es = c->precision == LBM_F64 ? 8 : 4;
+    const size_t n = (size_t)d.cells;
+    const bool dev = is_device_ptr(rho) && is_device_ptr(u);
+    void *drho = rho, *du = u;
+    if (!dev) {
+        int rc = ensure_scratch(c, 4 * n * es);
+        if (rc) return rc;
+        drho = c->scratch;
+        du = (char *)c->scratch + n * es;
+    }
+    const StepArgs a = make_args(c, c->t);
+    int rc = dispatch(c, [&](auto P) {
+        return lbm::launch_moments<decltype(P)::value>(c->wall, (int)(c->t & 1), a, d, m, drho, du, c->stream);
+    });
+    if (rc) return rc;
+    if (!dev) {
+        LBM_CUDA(c, cudaMemcpyAsync(rho, drho, n * es, cudaMemcpyDefault, c->stream));
+        LBM_CUDA(c, cudaMemcpyAsync(u, du, 3 * n * es, cudaMemcpyDefault, c->stream));
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx *c, double *f) {
+    if (!c || !f) return LBM_EINVAL;
+    const int m = c->sel;
+    const Member &d = c->hm[m];
+    const size_t bytes = (size_t)27 * d.cells * sizeof(double);
+    const bool dev = is_device_ptr(f);
+    double *df = f;
+    if (!dev) {
+        int rc = ensure_scratch(c, bytes);
+        if (rc) return rc;
+        df = (double *)c->scratch;
+    }
+    const StepArgs a = make_args(c, c->t);
+    int rc = dispatch(c, [&](auto P) {
+        return lbm::launch_get_pops<decltype(P)::value>(c->wall, (int)(c->t & 1), a, d, m, df, c->stream);
+    });
+    if (rc) return rc;
+    if (!dev) {
+        LBM_CUDA(c, cudaMemcpyAsync(f, df, bytes, cudaMemcpyDefault, c->stream));
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx *c, const double *f) {
+    if (!c || !f) return LBM_EINVAL;
+    const int m = c->sel;
+    const Member &d = c->hm[m];
+    const size_t bytes = (size_t)27 * d.cells * sizeof(double);
+    const bool dev = is_device_ptr(f);
+    const double *df = f;
+    if (!dev) {
+        int rc = ensure_scratch(c, bytes);
+        if (rc) return rc;
+        LBM_CUDA(c, cudaMemcpyAsync(c->scratch, f, bytes, cudaMemcpyDefault, c->stream));
+        df = (const double *)c->scratch;
+    }
+    const StepArgs a = make_args(c, c->t);
+    int rc = dispatch(c, [&](auto P) {
+        return lbm::launch_set_pops<decltype(P)::value>(c->wall, (int)(c->t & 1), a, d, m, df, c->stream);
+    });
+    if (rc) return rc;
+    c->mass0_valid[m] = false;
+    if (!dev) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_get_raw(lbm_ctx *c, void *buf, size_t bytes) {
+    if (!c || !buf) return LBM_EINVAL;
+    const size_t need = (size_t)27 * c->stride * c->esize;
+    if (bytes != need) return set_err(c, LBM_EINVAL, "raw buffer must hold exactly %zu bytes", need);
+    LBM_CUDA(c, cudaMemcpyAsync(buf, c->pops, need, cudaMemcpyDefault, c->stream));
+    if (!is_device_ptr(buf)) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_set_raw(lbm_ctx *c, const void *buf, size_t bytes) {
+    if (!c || !buf) return LBM_EINVAL;
+    const size_t need = (size_t)27 * c->stride * c->esize;
+    if (bytes != need) return set_err(c, LBM_EINVAL, "raw buffer must hold exactly %zu bytes", need);
+    LBM_CUDA(c, cudaMemcpyAsync(c->pops, buf, need, cudaMemcpyDefault, c->stream));
+    if (!is_device_ptr(buf)) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_reduce(lbm_ctx *c, double *out) {
+    if (!c || !out) return LBM_EINVAL;
+    return reduce_member(c, c->sel, out);
+}
+
+int lbm_stats_enable(lbm_ctx *c, int32_t every) {
+    if (!c) return LBM_EINVAL;
+    if (every < 1) return set_err(c, LBM_EINVAL, "stats interval must be >= 1");
+    if (!c->stats) {
+        cudaError_t e = cudaMalloc((void **)&c->stats, sizeof(double) * 4 * c->stride);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->stats = nullptr;
+            return set_err(c, LBM_ENOMEM, "cannot allocate statistics accumulators");
+        }
+    }
+    LBM_CUDA(c, cudaMemsetAsync(c->stats, 0, sizeof(double) * 4 * c->stride, c->stream));
+    c->stats_every = every;
+    c->stats_count = 0;
+    return LBM_OK;
+}
+
+int lbm_stats_get(lbm_ctx *c, double *acc, int64_t *count) {
+    if (!c || !acc) return LBM_EINVAL;
+    if (!c->stats) return set_err(c, LBM_EINVAL, "statistics are not enabled");
+    const Member &d = c->hm[c->sel];
+    LBM_CUDA(c, cudaMemcpy2DAsync(acc, (size_t)d.cells * sizeof(double), c->stats + d.off,
+                                  (size_t)c->stride * sizeof(double), (size_t)d.cells * sizeof(double), 4,
+                                  cudaMemcpyDefault, c->stream));
+    if (!is_device_ptr(acc)) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (count) *count = c->stats_count;
+    return LBM_OK;
+}
+
+int lbm_modes(lbm_ctx *c, const lbm_modes_cfg *cfg, double *E) {
+    if (!c || !cfg || !E) return LBM_EINVAL;
+    const int m = c->sel;
+    const Member &d = c->hm[m];
+    if (d.geometry != LBM_PIPE) return set_err(c, LBM_EINVAL, "modes need a pipe");
+    if (cfg->n_sections < 1 || cfg->n_sections > d.nz) return set_err(c, LBM_EINVAL, "n_sections must be in 1..nz");
+    if (cfg->n_rings < 1 || cfg->n_rings > 16) return set_err(c, LBM_EINVAL, "n_rings must be in 1..16");
+    if (cfg->n_theta < 8 || cfg->n_theta > 4096) return set_err(c, LBM_EINVAL, "n_theta must be in 8..4096");
+    if (cfg->n_modes < 0 || cfg->n_modes >= cfg->n_theta) return set_err(c, LBM_EINVAL, "n_modes must be in 0..n_theta-1");
+    lbm::ModesArgs ma;
+    std::memset(&ma, 0, sizeof ma);
+    ma.n_sections = cfg->n_sections;
+    ma.n_rings = cfg->n_rings;
+    ma.n_theta = cfg->n_theta;
+    ma.n_modes = cfg->n_modes;
+    for (int j = 0; j < cfg->n_rings; ++j) {
+        const double rr = cfg->r_over_R[j];
+        if (!(rr > 0.0) || rr * d.R + 1.5 >= 0.5 * std::min(d.nx, d.ny))
+            return set_err(c, LBM_EINVAL, "ring %d: r_over_R must put the ring inside the box", j);
+        ma.r_over_R[j] = rr;
+    }
+    const size_t bytes = sizeof(double) * cfg->n_sections * cfg->n_rings * (cfg->n_modes + 1);
+    const bool dev = is_device_ptr(E);
+    double *dE = E;
+    if (!dev) {
+        int rc = ensure_scratch(c, bytes);
+        if (rc) return rc;
+        dE = (double *)c->scratch;
+    }
+    const StepArgs a = make_args(c, c->t);
+    int rc = dispatch(c, [&](auto P) {
+        return lbm::launch_modes<decltype(P)::value>(c->wall, (int)(c->t & 1), a, d, m, ma, dE, c->stream);
+    });
+    if (rc) return rc;
+    if (!dev) {
+        LBM_CUDA(c, cudaMemcpyAsync(E, dE, bytes, cudaMemcpyDefault, c->stream));
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_every, double *J, double *dJ_dgz,
+                double *dJ_domega) {
+    (void)T; (void)objective; (void)checkpoint_every; (void)J; (void)dJ_dgz; (void)dJ_domega;
+    if (!c) return LBM_EINVAL;
+    return set_err(c, LBM_EUNSUPPORTED, "adjoint not available in this build");
+}
+
+int lbm_profile_enable(lbm_ctx *c, int32_t on) {
+    if (!c) return LBM_EINVAL;
+    c->prof = on != 0;
+    return LBM_OK;
+}
+
+int lbm_profile_read(lbm_ctx *c, double *ms, int64_t *launches) {
+    if (!c) return LBM_EINVAL;
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    double total = 0;
+    for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+        float x = 0;
+        LBM_CUDA(c, cudaEventElapsedTime(&x, c->ev[k], c->ev[k + 1]));
+        total += x;
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = (int64_t)(c->ev_used / 2);
+    c->ev_used = 0;
+    return LBM_OK;
+}
+
+int lbm_fluid_mask(lbm_ctx *c, uint8_t *mask) {
+    if (!c || !mask) return LBM_EINVAL;
+    const Member &d = c->hm[c->sel];
+    for (int y = 0; y < d.ny; ++y)
+        for (int x = 0; x < d.nx; ++x) mask[(size_t)y * d.nx + x] = col_fluid_host(d, x, y) ? 1 : 0;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,484 @@
+// lbm_device.cuh -- device building blocks of the D3Q27 MRT step.
+//
+// * Lattice (Appendix A): velocity order, opposite directions, weights.
+// * Storage traits: populations are stored as f_i - w_i in double, float, half
+//   (scaled by 2^s) or bfloat16; arithmetic runs in double or float.
+// * The single-buffer AA access pattern: an even step reads and writes the cell's
+//   own slots (slot i read as f_i, f*_i written to slot ibar); an odd step pulls
+//   f_i from slot ibar of x - c_i and pushes f*_i to slot i of x + c_i.  Both touch
+//   each slot exactly once, so the update is in place and race-free.  Wall links
+//   (x - c_i solid) read and write the cell's own slot instead, which realises
+//   half-way bounce-back; Bouzidi links add the interpolation of Eqs. (fbc1)-(fbc2)
+//   on top of the same slots.
+// * The collision of Eqs. (collision), (m*), (k*f*) in closed form.  With Lambda =
+//   diag[1,1,1,1,omega x5,1 x18] every non-shear moment leaves the collision at
+//   m^eq + R/2, so f* = f^eq + (1/2) g . grad_u f^eq + (1 - omega) sum_{k=4..8} C_k
+//   (m_k - m_k^eq + R_k / 2), where C_k is column k of (M^T)^{-1} (nonzero only on
+//   the 4 or 6 populations with the matching second-order velocity product).  The
+//   sixth-order Hermite equilibrium factorises on D3Q27 as rho w_i psi(c_ix, u_x)
+//   psi(c_iy, u_y) psi(c_iz, u_z), psi(0,u)/psi(0,0) = 1 - 3u^2/2 and
+//   psi(+-1,u)/psi(+-1,0) = 1 +- 3u + 3u^2, which is what is evaluated.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <type_traits>
+
+#include "lbm.h"
+
+namespace lbm {
+
+// ---- lattice, Appendix A ----------------------------------------------------------
+constexpr int Q = 27;
+__host__ __device__ constexpr int cx_of(int i) {
+    constexpr int v[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1};
+    return v[i];
+}
+__host__ __device__ constexpr int cy_of(int i) {
+    constexpr int v[27] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, 1, -1, -1, 1, 1, -1, -1};
+    return v[i];
+}
+__host__ __device__ constexpr int cz_of(int i) {
+    constexpr int v[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 1, 1, 1, 1, -1, -1, -1, -1};
+    return v[i];
+}
+__host__ __device__ constexpr int opp_of(int i) {
+    for (int j = 0; j < 27; ++j)
+        if (cx_of(j) == -cx_of(i) && cy_of(j) == -cy_of(i) && cz_of(j) == -cz_of(i)) return j;
+    return -1;
+}
+// Eq. (omegas): w0 = 8/27, w0/4 on faces, w0/16 on edges, w0/64 on corners.
+__host__ __device__ constexpr double w_of(int i) {
+    return i == 0 ? 8.0 / 27.0 : (i <= 6 ? 2.0 / 27.0 : (i <= 18 ? 1.0 / 54.0 : 1.0 / 216.0));
+}
+// in-plane neighbourhood bit of (cx, cy): bit (cy + 1) * 3 + (cx + 1)
+__host__ __device__ constexpr int nbit(int cx, int cy) { return (cy + 1) * 3 + (cx + 1); }
+
+template <int I, int N, class F>
+__device__ __forceinline__ void sfor(F &&f) {
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        sfor<I + 1, N>(f);
+    }
+}
+
+// ---- storage ------------------------------------------------------------------------
+template <int P> struct Storage;
+template <> struct Storage<LBM_F64> {
+    using T = double; using R = double;
+    static __device__ __forceinline__ R ld(const T *p, R) { return *p; }
+    static __device__ __forceinline__ void st(T *p, R v, R) { *p = v; }
+};
+template <> struct Storage<LBM_F32> {
+    using T = float; using R = float;
+    static __device__ __forceinline__ R ld(const T *p, R) { return *p; }
+    static __device__ __forceinline__ void st(T *p, R v, R) { *p = v; }
+};
+template <> struct Storage<LBM_F16S> {
+    using T = __half; using R = float;
+    static __device__ __forceinline__ R ld(const T *p, R inv_scale) { return __half2float(*p) * inv_scale; }
+    static __device__ __forceinline__ void st(T *p, R v, R scale) { *p = __float2half_rn(v * scale); }
+};
+template <> struct Storage<LBM_BF16> {
+    using T = __nv_bfloat16; using R = float;
+    static __device__ __forceinline__ R ld(const T *p, R) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(T *p, R v, R) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---- per-member description (host fills, device reads) ---------------------------------
+struct Member {
+    int32_t nx, ny, nz, geometry;
+    int64_t off;        // first cell of this member inside each population plane
+    int64_t cells;      // nx * ny * nz
+    int64_t block0;     // first block of this member in a flat launch
+    int64_t n_fluid;
+    int64_t d2max;      // pipe: fluid iff (2x-nx+1)^2 + (2y-ny+1)^2 <= d2max
+    double R, omega;
+    double g[3];
+    // trigger force, Eq. (TurbForce)
+    int32_t trig, n_modes, kz, pad0;
+    int32_t k_theta[LBM_MAX_TRIGGER_MODES];
+    double amp[LBM_MAX_TRIGGER_MODES];     // h * A0 * weight
+    double cph[LBM_MAX_TRIGGER_MODES], sph[LBM_MAX_TRIGGER_MODES];
+    double kappa, l0, l, period;
+    int64_t t_end;
+    const void *gz_field;
+    uint32_t nx_mul, nx_shr, ny_mul, ny_shr;   // magic division by nx and ny
+};
+
+// Unsigned division by a fixed divisor d >= 1 for n < 2^31: q = umulhi(n, mul) >> shr.
+inline void fastdiv_setup(uint32_t d, uint32_t &mul, uint32_t &shr) {
+    uint32_t s = 0;
+    while ((1ull << s) < d) ++s;
+    // mul = ceil(2^(32+s) / d); exact for n < 2^31 when d < 2^31
+    uint64_t m = ((1ull << (32 + s)) + d - 1) / d;
+    if (m >= (1ull << 32)) { // only for d == 1
+        mul = 0; shr = 0xFFFFFFFFu; return;
+    }
+    mul = (uint32_t)m; shr = s;
+}
+__device__ __forceinline__ uint32_t fastdiv(uint32_t n, uint32_t mul, uint32_t shr) {
+    return shr == 0xFFFFFFFFu ? n : (__umulhi(n, mul) >> shr);
+}
+
+struct StepArgs {
+    void *pops;               // [27][stride] storage elements
+    int64_t stride;           // cells per population plane (all members)
+    const Member *members;    // device array
+    int32_t n_members;
+    int32_t nblocks_total;
+    int64_t t;                // index of the step being taken
+    float f16_scale, f16_inv;
+    double *stats;            // [4][stride] FP64 accumulators (sample steps)
+    double st[LBM_MAX_MEMBERS];      // sin(2 pi t / T) per member (0 when off)
+    int32_t block0[LBM_MAX_MEMBERS + 1];
+};
+
+__device__ __forceinline__ int find_member(const StepArgs &a, int blk) {
+    int lo = 0, hi = a.n_members - 1;
+    while (lo < hi) {          // largest m with block0[m] <= blk
+        int mid = (lo + hi + 1) >> 1;
+        if (a.block0[mid] <= blk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---- geometry --------------------------------------------------------------------------
+struct CellPos {
+    int x, y, z;
+    int64_t cell;            // index inside the population plane (member offset added)
+    int32_t ox[3], oy[3], oz[3]; // neighbour offsets for c = -1, 0, +1 (periodic)
+    uint32_t nb;             // in-plane fluid mask of the 3x3 neighbourhood
+};
+
+__device__ __forceinline__ bool col_fluid(const Member &d, int x, int y) {
+    if (d.geometry == LBM_BOX) return true;
+    int64_t X = 2 * (int64_t)x - d.nx + 1, Y = 2 * (int64_t)y - d.ny + 1;
+    return X * X + Y * Y <= d.d2max;
+}
+
+__device__ __forceinline__ void cell_setup(const Member &d, uint32_t local, CellPos &p) {
+    uint32_t q = fastdiv(local, d.nx_mul, d.nx_shr);
+    p.x = (int)(local - q * (uint32_t)d.nx);
+    p.z = (int)fastdiv(q, d.ny_mul, d.ny_shr);
+    p.y = (int)(q - (uint32_t)p.z * (uint32_t)d.ny);
+    p.cell = d.off + (int64_t)local;
+    const int32_t nx = d.nx, nxy = d.nx * d.ny;
+    p.ox[0] = p.x == 0 ? nx - 1 : -1;
+    p.ox[1] = 0;
+    p.ox[2] = p.x == nx - 1 ? -(nx - 1) : 1;
+    p.oy[0] = p.y == 0 ? (d.ny - 1) * nx : -nx;
+    p.oy[1] = 0;
+    p.oy[2] = p.y == d.ny - 1 ? -(d.ny - 1) * nx : nx;
+    p.oz[0] = p.z == 0 ? (d.nz - 1) * nxy : -nxy;
+    p.oz[1] = 0;
+    p.oz[2] = p.z == d.nz - 1 ? -(d.nz - 1) * nxy : nxy;
+    uint32_t nb = 0;
+    if (d.geometry == LBM_BOX) {
+        nb = 0x1FF;
+    } else {
+#pragma unroll
+        for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
+            for (int cx = -1; cx <= 1; ++cx)
+                nb |= (uint32_t)col_fluid(d, p.x + cx, p.y + cy) << nbit(cx, cy);
+    }
+    p.nb = nb;
+}
+
+template <int I>
+__device__ __forceinline__ int32_t nb_offset(const CellPos &p) {   // x + c_I
+    return p.ox[cx_of(I) + 1] + p.oy[cy_of(I) + 1] + p.oz[cz_of(I) + 1];
+}
+template <int I>
+__device__ __forceinline__ int32_t src_offset(const CellPos &p) {  // x - c_I
+    return p.ox[1 - cx_of(I)] + p.oy[1 - cy_of(I)] + p.oz[1 - cz_of(I)];
+}
+template <int I>
+__device__ __forceinline__ bool src_is_fluid(const CellPos &p) {
+    return (p.nb >> nbit(-cx_of(I), -cy_of(I))) & 1u;
+}
+template <int I>
+__device__ __forceinline__ bool dst_is_fluid(const CellPos &p) {
+    return (p.nb >> nbit(cx_of(I), cy_of(I))) & 1u;
+}
+
+// ---- Bouzidi link coefficients, Eqs. (fbc1)-(fbc2) ---------------------------------------
+// For a wall-pointing direction J of a fluid cell (x + c_J solid), the population
+// returning in direction Jbar is A f*_J(x) + B f*_Jbar(x) + C f*_J(x - c_J).
+template <class R>
+struct BLink { R A, B, C; };
+
+template <class R, int J>
+__device__ __forceinline__ BLink<R> bouzidi_link(const Member &d, const CellPos &p) {
+    BLink<R> b{R(1), R(0), R(0)};
+    const R px = R(0.5) * R(2 * p.x - d.nx + 1), py = R(0.5) * R(2 * p.y - d.ny + 1);
+    constexpr int cx = cx_of(J), cy = cy_of(J);
+    const R a = R(cx * cx + cy * cy);
+    const R bb = px * R(cx) + py * R(cy);
+    const R cc = px * px + py * py - R(d.R) * R(d.R);
+    const R delta = (-bb + sqrt(bb * bb - a * cc)) / a;
+    if (delta >= R(0.5)) {
+        b.A = R(1) / (R(2) * delta);
+        b.B = (R(2) * delta - R(1)) / (R(2) * delta);
+    } else if ((p.nb >> nbit(-cx, -cy)) & 1u) {   // x_ff = x - c_J is fluid
+        b.A = R(2) * delta;
+        b.C = R(1) - R(2) * delta;
+    }
+    return b;
+}
+
+// ---- loading and storing the 27 populations of a cell ------------------------------------
+// PAR 0: natural layout (after an odd step); PAR 1: reversed layout (after an even step).
+template <int P, int PAR, int WALL>
+__device__ __forceinline__ void load_pops(const StepArgs &a, const Member &d, const CellPos &p,
+                                          typename Storage<P>::R (&v)[Q]) {
+    using S = Storage<P>;
+    using T = typename S::T;
+    using R = typename S::R;
+    const T *base = static_cast<const T *>(a.pops);
+    const R inv = (R)a.f16_inv;
+    sfor<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int ib = opp_of(i);
+        if constexpr (PAR == 0) {
+            v[i] = S::ld(base + (int64_t)i * a.stride + p.cell, inv);
+        } else {
+            if constexpr (WALL == LBM_FULLWAY || (cx_of(i) == 0 && cy_of(i) == 0)) {
+                v[i] = S::ld(base + (int64_t)ib * a.stride + p.cell + src_offset<i>(p), inv);
+            } else {
+                if (src_is_fluid<i>(p))
+                    v[i] = S::ld(base + (int64_t)ib * a.stride + p.cell + src_offset<i>(p), inv);
+                else
+                    v[i] = S::ld(base + (int64_t)i * a.stride + p.cell, inv);
+            }
+        }
+    });
+    if constexpr (WALL == LBM_BOUZIDI) {
+        if (p.nb != 0x1FFu) {
+            sfor<0, Q>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                if constexpr (cx_of(j) != 0 || cy_of(j) != 0) {
+                    if (!dst_is_fluid<j>(p)) {
+                        BLink<R> b = bouzidi_link<R, j>(d, p);
+                        v[opp_of(j)] += b.C * v[j];
+                    }
+                }
+            });
+        }
+    }
+}
+
+template <int P, int PAR, int WALL>
+__device__ __forceinline__ void store_pops(const StepArgs &a, const Member &d, const CellPos &p,
+                                           typename Storage<P>::R (&v)[Q]) {
+    using S = Storage<P>;
+    using T = typename S::T;
+    using R = typename S::R;
+    T *base = static_cast<T *>(a.pops);
+    const R sc = (R)a.f16_scale;
+    // Bouzidi: the value reflected into slot Jbar becomes A f*_J + B f*_Jbar
+    R out[Q];
+    sfor<0, Q>([&](auto ic) { constexpr int i = decltype(ic)::value; out[i] = v[i]; });
+    if constexpr (WALL == LBM_BOUZIDI) {
+        if (p.nb != 0x1FFu) {
+            sfor<0, Q>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                if constexpr (cx_of(j) != 0 || cy_of(j) != 0) {
+                    if (!dst_is_fluid<j>(p)) {
+                        BLink<R> b = bouzidi_link<R, j>(d, p);
+                        out[j] = b.A * v[j] + b.B * v[opp_of(j)];
+                    }
+                }
+            });
+        }
+    }
+    sfor<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int ib = opp_of(i);
+        if constexpr (PAR == 0) {
+            S::st(base + (int64_t)ib * a.stride + p.cell, out[i], sc);
+        } else {
+            if constexpr (WALL == LBM_FULLWAY || (cx_of(i) == 0 && cy_of(i) == 0)) {
+                S::st(base + (int64_t)i * a.stride + p.cell + nb_offset<i>(p), out[i], sc);
+            } else {
+                if (dst_is_fluid<i>(p))
+                    S::st(base + (int64_t)i * a.stride + p.cell + nb_offset<i>(p), out[i], sc);
+                else
+                    S::st(base + (int64_t)ib * a.stride + p.cell, out[i], sc);
+            }
+        }
+    });
+}
+
+// ---- acceleration g(x, t), Sec. II.B ----------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void acceleration(const Member &d, const CellPos &p, int64_t t, double st,
+                                             R &gx, R &gy, R &gz) {
+    gx = (R)d.g[0];
+    gy = (R)d.g[1];
+    gz = (R)d.g[2];
+    if (d.gz_field != nullptr) {
+        const int64_t local = p.cell - d.off;
+        gz += (R)(static_cast<const R *>(d.gz_field)[local]);
+    }
+    if (d.trig && t < d.t_end && d.geometry == LBM_PIPE) {
+        const R px = R(0.5) * R(2 * p.x - d.nx + 1), py = R(0.5) * R(2 * p.y - d.ny + 1);
+        const R r = sqrt(px * px + py * py);
+        const R Rr = (R)d.R, l0 = (R)d.l0, l = (R)d.l;
+        if (r >= Rr - l0 - l && r <= Rr - l0 && r > R(0)) {
+            const R ir = R(1) / r;
+            const R ct = px * ir, sn = py * ir;
+            const R L = (R)d.nz;
+            R sa, ca, sz, cz;
+            sincospi(R(2) * (Rr - r - l0) / l, &sa, &ca);
+            sincospi(R(2) * R(d.kz) * R(p.z) / L, &sz, &cz);
+            const R s = (R)st;
+            const R kap = (R)d.kappa;
+            const R twopi = R(6.283185307179586476925286766559);
+            R Fr = 0, Ft = 0, Fz = 0;
+            // cos(k theta), sin(k theta) by repeated multiplication with e^{i theta}
+            R ck = 1, sk = 0;
+            int k = 0;
+            for (int q = 0; q < d.n_modes; ++q) {
+                const int kt = d.k_theta[q];
+                while (k < kt) {
+                    const R c2 = ck * ct - sk * sn;
+                    sk = sk * ct + ck * sn;
+                    ck = c2;
+                    ++k;
+                }
+                if (k > kt) {   // modes given out of order: restart
+                    ck = 1; sk = 0; k = 0;
+                    while (k < kt) { const R c2 = ck * ct - sk * sn; sk = sk * ct + ck * sn; ck = c2; ++k; }
+                }
+                const R cph = (R)d.cph[q], sph = (R)d.sph[q];
+                const R cang = ck * cph - sk * sph;
+                const R sang = sk * cph + ck * sph;
+                const R A = (R)d.amp[q] * s;
+                Fr -= A * kap * (Rr * ir) * (R(d.kz) * l / L) * (R(1) - ca) * cz * cang;
+                Ft += A * (R(1) - kap) * (R(d.kz) / R(kt)) * (twopi * Rr / L) * sa * cz * sang;
+                Fz -= A * (Rr * ir) * sa * sz * cang;
+            }
+            gx += Fr * ct - Ft * sn;
+            gy += Fr * sn + Ft * ct;
+            gz += Fz;
+        }
+    }
+}
+
+// ---- collision ------------------------------------------------------------------------------
+template <class R>
+struct Macro { R drho, rho, ux, uy, uz; };
+
+template <class R>
+__device__ __forceinline__ Macro<R> macroscopic(const R (&v)[Q], R gx, R gy, R gz) {
+    R drho = 0, jx = 0, jy = 0, jz = 0;
+    sfor<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        drho += v[i];
+        if constexpr (cx_of(i) == 1) jx += v[i];
+        if constexpr (cx_of(i) == -1) jx -= v[i];
+        if constexpr (cy_of(i) == 1) jy += v[i];
+        if constexpr (cy_of(i) == -1) jy -= v[i];
+        if constexpr (cz_of(i) == 1) jz += v[i];
+        if constexpr (cz_of(i) == -1) jz -= v[i];
+    });
+    Macro<R> m;
+    m.drho = drho;
+    m.rho = R(1) + drho;
+    const R ir = R(1) / m.rho;
+    m.ux = jx * ir + R(0.5) * gx;
+    m.uy = jy * ir + R(0.5) * gy;
+    m.uz = jz * ir + R(0.5) * gz;
+    return m;
+}
+
+// One-axis factors of the product-form equilibrium (see the file header):
+// dl[c+1] = psi_hat(c,u) - 1, hd[c+1] = (g/2) d psi_hat / du.
+template <class R>
+__device__ __forceinline__ void axis_factors(R u, R g, R (&dl)[3], R (&hd)[3]) {
+    const R u2 = u * u;
+    dl[1] = R(-1.5) * u2;
+    dl[0] = R(3) * u2 - R(3) * u;
+    dl[2] = R(3) * u2 + R(3) * u;
+    const R hg = R(0.5) * g;
+    hd[1] = hg * (R(-3) * u);
+    hd[0] = hg * (R(6) * u - R(3));
+    hd[2] = hg * (R(6) * u + R(3));
+}
+
+// In-place collision of one fluid cell; v holds f - w on entry and f* - w on exit.
+template <class R>
+__device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega) {
+    const Macro<R> mm = macroscopic<R>(v, gx, gy, gz);
+    const R rho = mm.rho, ux = mm.ux, uy = mm.uy, uz = mm.uz;
+    // raw second moments m4..m8 (the rest weights contribute nothing to them)
+    R m4 = 0, m5 = 0, m6 = 0, m7 = 0, m8 = 0;
+    sfor<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int xy = cx_of(i) * cy_of(i), xz = cx_of(i) * cz_of(i), yz = cy_of(i) * cz_of(i);
+        constexpr int d7 = cx_of(i) * cx_of(i) - cy_of(i) * cy_of(i);
+        constexpr int d8 = cx_of(i) * cx_of(i) - cz_of(i) * cz_of(i);
+        if constexpr (xy == 1) m4 += v[i];
+        if constexpr (xy == -1) m4 -= v[i];
+        if constexpr (xz == 1) m5 += v[i];
+        if constexpr (xz == -1) m5 -= v[i];
+        if constexpr (yz == 1) m6 += v[i];
+        if constexpr (yz == -1) m6 -= v[i];
+        if constexpr (d7 == 1) m7 += v[i];
+        if constexpr (d7 == -1) m7 -= v[i];
+        if constexpr (d8 == 1) m8 += v[i];
+        if constexpr (d8 == -1) m8 -= v[i];
+    });
+    // (1 - omega)(m_k - m_k^eq + R_k / 2), k = 4..8, with the printed m^eq and R
+    const R om1 = R(1) - omega;
+    const R a4 = om1 * (m4 - rho * ux * uy + R(0.5) * rho * (gy * ux + gx * uy));
+    const R a5 = om1 * (m5 - rho * ux * uz + R(0.5) * rho * (gz * ux + gx * uz));
+    const R a6 = om1 * (m6 - rho * uy * uz + R(0.5) * rho * (gz * uy + gy * uz));
+    const R a7 = om1 * (m7 - rho * (ux * ux - uy * uy) + rho * (gx * ux - gy * uy));
+    const R a8 = om1 * (m8 - rho * (ux * ux - uz * uz) + rho * (gx * ux - gz * uz));
+    const R s12 = (a7 + a8) * R(1.0 / 6.0);
+    const R s34 = a8 * R(1.0 / 6.0) - a7 * R(1.0 / 3.0);
+    const R s56 = a7 * R(1.0 / 6.0) - a8 * R(1.0 / 3.0);
+    const R q4 = R(0.25) * a4, q5 = R(0.25) * a5, q6 = R(0.25) * a6;
+
+    R dx[3], hx[3], dy[3], hy[3], dz[3], hz[3];
+    axis_factors<R>(ux, gx, dx, hx);
+    axis_factors<R>(uy, gy, dy, hy);
+    axis_factors<R>(uz, gz, dz, hz);
+    // per (cx, cy) pair: Dxy = psi_x psi_y - 1 and the x/y force part
+    R Dxy[3][3], Fxy[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            Dxy[a][b] = dx[a] + dy[b] + dx[a] * dy[b];
+            Fxy[a][b] = hx[a] * (R(1) + dy[b]) + hy[b] * (R(1) + dx[a]);
+        }
+    const R drho = mm.drho;
+    sfor<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int a = cx_of(i) + 1, b = cy_of(i) + 1, c = cz_of(i) + 1;
+        const R dxy = Dxy[a][b];
+        const R axy = R(1) + dxy;
+        const R pm1 = dxy + dz[c] * axy;                       // psi_x psi_y psi_z - 1
+        const R frc = Fxy[a][b] * (R(1) + dz[c]) + hz[c] * axy; // (1/2) g . grad psi
+        R f = R(w_of(i)) * (drho + rho * (pm1 + frc));
+        if constexpr (i == 1 || i == 2) f += s12;
+        if constexpr (i == 3 || i == 4) f += s34;
+        if constexpr (i == 5 || i == 6) f += s56;
+        if constexpr (i == 7 || i == 10) f += q4;
+        if constexpr (i == 8 || i == 9) f -= q4;
+        if constexpr (i == 11 || i == 14) f += q5;
+        if constexpr (i == 12 || i == 13) f -= q5;
+        if constexpr (i == 15 || i == 18) f += q6;
+        if constexpr (i == 16 || i == 17) f -= q6;
+        v[i] = f;
+    });
+    return mm;
+}
+
+}  // namespace lbm

@@ -1,0 +1,47 @@
+// lbm_internal.h -- host-side interface between the C ABI (lbm_api.cu) and the
+// per-precision kernel translation units (lbm_f64.cu, lbm_f32.cu, ...).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+struct ModesArgs {
+    int32_t n_sections, n_rings, n_theta, n_modes;
+    double r_over_R[16];
+};
+
+// Every launcher enqueues on `s` and returns the launch status.
+// Step kernel over all members (flat grid of a.nblocks_total blocks of `block` threads).
+template <int P>
+cudaError_t launch_step(int wall, int parity, bool stats, const StepArgs &a, int block, cudaStream_t s);
+
+// Per-member kernels: member m of a.members (host copy hm for sizes).
+template <int P>
+cudaError_t launch_moments(int wall, int parity, const StepArgs &a, const Member &hm, int m,
+                           void *rho, void *u, cudaStream_t s);
+template <int P>
+cudaError_t launch_get_pops(int wall, int parity, const StepArgs &a, const Member &hm, int m,
+                            double *f, cudaStream_t s);
+template <int P>
+cudaError_t launch_set_pops(int wall, int parity, const StepArgs &a, const Member &hm, int m,
+                            const double *f, cudaStream_t s);
+template <int P>
+cudaError_t launch_init(int wall, const StepArgs &a, const Member &hm, int m, int profile, double noise_amp,
+                        uint64_t seed, const double *rho, const double *u, cudaStream_t s);
+// Block partials (5 doubles per block) then a one-block final pass into out[5] (device).
+template <int P>
+cudaError_t launch_reduce(int wall, int parity, const StepArgs &a, const Member &hm, int m,
+                          double *partials, int n_partials_max, double *out, cudaStream_t s);
+template <int P>
+cudaError_t launch_modes(int wall, int parity, const StepArgs &a, const Member &hm, int m,
+                         const ModesArgs &ma, double *E, cudaStream_t s);
+
+constexpr int STEP_BLOCK_HOST = 256;   // threads per block of the step kernel
+constexpr int REDUCE_BLOCK = 256;
+constexpr int REDUCE_MAX_BLOCKS = 1216;   // 8 resident blocks x 152 SMs
+
+}  // namespace lbm

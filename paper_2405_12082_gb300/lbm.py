@@ -1,0 +1,391 @@
+"""ctypes binding of liblbm.so (include/lbm.h): the same names, argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts Python values,
+numpy arrays and torch tensors into the C structs and pointers of the ABI and turns
+non-zero status codes into LbmError.  Importing it raises if the library has not
+been built (there is no CPU fallback): call __graft_entry__.build() or
+``python -m paper_2405_12082_gb300.build``.
+"""
+import ctypes
+import math
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbm.so")
+
+# ---- constants (include/lbm.h) -------------------------------------------------------
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA = 0, -1, -2, -3
+LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_EUNSUPPORTED = -4, -5, -6
+LBM_F64, LBM_F32, LBM_F16S, LBM_BF16 = 0, 1, 2, 3
+LBM_PIPE, LBM_BOX = 0, 1
+LBM_HALFWAY, LBM_FULLWAY, LBM_BOUZIDI = 0, 1, 2
+LBM_REST, LBM_LAMINAR, LBM_LOGLAW = 0, 1, 2
+LBM_J_UBULK, LBM_J_WSS = 0, 1
+LBM_MAX_TRIGGER_MODES = 8
+LBM_MAX_MEMBERS = 64
+
+PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16": LBM_BF16}
+WALLS = {"halfway": LBM_HALFWAY, "fullway": LBM_FULLWAY, "bouzidi": LBM_BOUZIDI}
+PROFILES = {"rest": LBM_REST, "laminar": LBM_LAMINAR, "loglaw": LBM_LOGLAW}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("lbm status %d: %s" % (status, message))
+        self.status = status
+
+
+class lbm_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("geometry", ctypes.c_int32), ("R", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("wall", ctypes.c_int32), ("f16_log2_scale", ctypes.c_int32)]
+
+
+class lbm_relax(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double)]
+
+
+class lbm_force(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_double * 3), ("trigger", ctypes.c_int32), ("n_modes", ctypes.c_int32),
+                ("k_theta", ctypes.c_int32 * LBM_MAX_TRIGGER_MODES),
+                ("weight", ctypes.c_double * LBM_MAX_TRIGGER_MODES),
+                ("phase", ctypes.c_double * LBM_MAX_TRIGGER_MODES),
+                ("A0", ctypes.c_double), ("kappa", ctypes.c_double), ("l0", ctypes.c_double),
+                ("l", ctypes.c_double), ("period", ctypes.c_double), ("h", ctypes.c_double),
+                ("kz", ctypes.c_int32), ("t_end", ctypes.c_int64), ("gz_field", ctypes.c_void_p)]
+
+
+class lbm_modes_cfg(ctypes.Structure):
+    _fields_ = [("n_sections", ctypes.c_int32), ("n_rings", ctypes.c_int32),
+                ("r_over_R", ctypes.c_double * 16), ("n_theta", ctypes.c_int32), ("n_modes", ctypes.c_int32)]
+
+
+class lbm_info(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int64), ("n_fluid", ctypes.c_int64), ("t", ctypes.c_int64),
+                ("population_bytes", ctypes.c_int64), ("n_members", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("launches", ctypes.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("liblbm.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, D, U64, SZ = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                               ctypes.c_uint64, ctypes.c_size_t)
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "lbm_create": [PP, ctypes.POINTER(lbm_grid), ctypes.POINTER(lbm_relax), ctypes.POINTER(lbm_force), P],
+        "lbm_ensemble_create": [PP, I32, ctypes.POINTER(lbm_grid), ctypes.POINTER(lbm_relax),
+                                ctypes.POINTER(lbm_force), P],
+        "lbm_set_stream": [P, P],
+        "lbm_select_member": [P, I32],
+        "lbm_get_info": [P, ctypes.POINTER(lbm_info)],
+        "lbm_set_relax": [P, ctypes.POINTER(lbm_relax)],
+        "lbm_set_force": [P, ctypes.POINTER(lbm_force)],
+        "lbm_init": [P, I32, D, U64],
+        "lbm_init_fields": [P, P, P],
+        "lbm_step": [P, I64],
+        "lbm_set_check": [P, I64, D],
+        "lbm_moments": [P, P, P],
+        "lbm_get_populations": [P, P],
+        "lbm_set_populations": [P, P],
+        "lbm_get_raw": [P, P, SZ],
+        "lbm_set_raw": [P, P, SZ],
+        "lbm_reduce": [P, P],
+        "lbm_stats_enable": [P, I32],
+        "lbm_stats_get": [P, P, ctypes.POINTER(ctypes.c_int64)],
+        "lbm_modes": [P, ctypes.POINTER(lbm_modes_cfg), P],
+        "lbm_adjoint": [P, I64, I32, I64, ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(ctypes.c_double)],
+        "lbm_profile_enable": [P, I32],
+        "lbm_profile_read": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+        "lbm_fluid_mask": [P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.lbm_free.argtypes = [P]
+    lib.lbm_free.restype = None
+    lib.lbm_last_error.argtypes = [P]
+    lib.lbm_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+LIB = _load()
+EXPORTED = ("lbm_create", "lbm_ensemble_create", "lbm_free", "lbm_last_error", "lbm_set_stream",
+            "lbm_select_member", "lbm_get_info", "lbm_set_relax", "lbm_set_force", "lbm_init",
+            "lbm_init_fields", "lbm_step", "lbm_set_check", "lbm_moments", "lbm_get_populations",
+            "lbm_set_populations", "lbm_get_raw", "lbm_set_raw", "lbm_reduce", "lbm_stats_enable",
+            "lbm_stats_get", "lbm_modes", "lbm_adjoint", "lbm_profile_enable", "lbm_profile_read",
+            "lbm_fluid_mask")
+
+
+# ---- marshalling helpers -----------------------------------------------------------------
+def ptr(x):
+    """Address of a torch tensor, numpy array, ctypes object or int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    return ctypes.addressof(x)
+
+
+def _check(ctx, rc):
+    if rc != LBM_OK:
+        raise LbmError(rc, LIB.lbm_last_error(ctx).decode())
+    return rc
+
+
+def make_grid(nx, ny, nz, R=0.0, geometry="pipe", precision="f32", wall="halfway", f16_log2_scale=0):
+    return lbm_grid(nx, ny, nz, LBM_PIPE if geometry == "pipe" else LBM_BOX, float(R),
+                    PRECISIONS[precision] if isinstance(precision, str) else precision,
+                    WALLS[wall] if isinstance(wall, str) else wall, f16_log2_scale)
+
+
+def make_force(g=(0.0, 0.0, 0.0), trigger=None, gz_field=None):
+    """trigger: dict with keys A0, kappa, kz, l0, l, period, h, t_end and modes =
+    [(k_theta, weight, phase), ...] (Eq. (TurbForce) per mode)."""
+    f = lbm_force()
+    for k in range(3):
+        f.g[k] = float(g[k])
+    if trigger is not None:
+        f.trigger = 1
+        modes = trigger["modes"]
+        f.n_modes = len(modes)
+        for q, (kt, wgt, ph) in enumerate(modes):
+            f.k_theta[q] = int(kt)
+            f.weight[q] = float(wgt)
+            f.phase[q] = float(ph)
+        f.A0 = float(trigger["A0"])
+        f.kappa = float(trigger["kappa"])
+        f.kz = int(trigger["kz"])
+        f.l0 = float(trigger["l0"])
+        f.l = float(trigger["l"])
+        f.period = float(trigger["period"])
+        f.h = float(trigger["h"])
+        f.t_end = int(trigger.get("t_end", 2 ** 62))
+    f.gz_field = ptr(gz_field)
+    return f
+
+
+def make_modes_cfg(n_sections, r_over_R, n_theta, n_modes):
+    c = lbm_modes_cfg()
+    c.n_sections = n_sections
+    c.n_rings = len(r_over_R)
+    for j, r in enumerate(r_over_R):
+        c.r_over_R[j] = float(r)
+    c.n_theta = n_theta
+    c.n_modes = n_modes
+    return c
+
+
+# ---- the ABI, name for name --------------------------------------------------------------
+def lbm_create(grid, relax, force=None, stream=None):
+    out = ctypes.c_void_p()
+    rc = LIB.lbm_create(ctypes.byref(out), ctypes.byref(grid), ctypes.byref(relax),
+                        ctypes.byref(force) if force is not None else None, ptr(stream))
+    _check(None, rc)
+    return out.value
+
+
+def lbm_ensemble_create(grids, relaxes, forces=None, stream=None):
+    n = len(grids)
+    G = (lbm_grid * n)(*grids)
+    Rl = (lbm_relax * n)(*relaxes)
+    F = (lbm_force * n)(*forces) if forces is not None else None
+    out = ctypes.c_void_p()
+    rc = LIB.lbm_ensemble_create(ctypes.byref(out), n, G, Rl, F, ptr(stream))
+    _check(None, rc)
+    return out.value
+
+
+def lbm_free(ctx):
+    LIB.lbm_free(ctx)
+
+
+def lbm_last_error(ctx):
+    return LIB.lbm_last_error(ctx).decode()
+
+
+def lbm_set_stream(ctx, stream):
+    return _check(ctx, LIB.lbm_set_stream(ctx, ptr(stream)))
+
+
+def lbm_select_member(ctx, member):
+    return _check(ctx, LIB.lbm_select_member(ctx, member))
+
+
+def lbm_get_info(ctx):
+    info = lbm_info()
+    _check(ctx, LIB.lbm_get_info(ctx, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in lbm_info._fields_}
+
+
+def lbm_set_relax(ctx, relax):
+    return _check(ctx, LIB.lbm_set_relax(ctx, ctypes.byref(relax)))
+
+
+def lbm_set_force(ctx, force):
+    return _check(ctx, LIB.lbm_set_force(ctx, ctypes.byref(force)))
+
+
+def lbm_init(ctx, profile=LBM_REST, noise_amp=0.0, seed=0):
+    profile = PROFILES[profile] if isinstance(profile, str) else profile
+    return _check(ctx, LIB.lbm_init(ctx, profile, float(noise_amp), int(seed)))
+
+
+def lbm_init_fields(ctx, rho, u):
+    return _check(ctx, LIB.lbm_init_fields(ctx, ptr(rho), ptr(u)))
+
+
+def lbm_step(ctx, n=1):
+    return _check(ctx, LIB.lbm_step(ctx, int(n)))
+
+
+def lbm_set_check(ctx, every, max_mass_drift):
+    return _check(ctx, LIB.lbm_set_check(ctx, int(every), float(max_mass_drift)))
+
+
+def lbm_moments(ctx, rho, u):
+    return _check(ctx, LIB.lbm_moments(ctx, ptr(rho), ptr(u)))
+
+
+def lbm_get_populations(ctx, f):
+    return _check(ctx, LIB.lbm_get_populations(ctx, ptr(f)))
+
+
+def lbm_set_populations(ctx, f):
+    return _check(ctx, LIB.lbm_set_populations(ctx, ptr(f)))
+
+
+def lbm_get_raw(ctx, buf, nbytes):
+    return _check(ctx, LIB.lbm_get_raw(ctx, ptr(buf), int(nbytes)))
+
+
+def lbm_set_raw(ctx, buf, nbytes):
+    return _check(ctx, LIB.lbm_set_raw(ctx, ptr(buf), int(nbytes)))
+
+
+def lbm_reduce(ctx):
+    out = (ctypes.c_double * 5)()
+    _check(ctx, LIB.lbm_reduce(ctx, ctypes.addressof(out)))
+    return list(out)
+
+
+def lbm_stats_enable(ctx, every):
+    return _check(ctx, LIB.lbm_stats_enable(ctx, int(every)))
+
+
+def lbm_stats_get(ctx, acc):
+    count = ctypes.c_int64()
+    _check(ctx, LIB.lbm_stats_get(ctx, ptr(acc), ctypes.byref(count)))
+    return count.value
+
+
+def lbm_modes(ctx, cfg, E):
+    return _check(ctx, LIB.lbm_modes(ctx, ctypes.byref(cfg), ptr(E)))
+
+
+def lbm_adjoint(ctx, T, objective, checkpoint_every, dJ_dgz):
+    J = ctypes.c_double()
+    dw = ctypes.c_double()
+    _check(ctx, LIB.lbm_adjoint(ctx, int(T), int(objective), int(checkpoint_every), ctypes.byref(J),
+                                ptr(dJ_dgz), ctypes.byref(dw)))
+    return J.value, dw.value
+
+
+def lbm_profile_enable(ctx, on):
+    return _check(ctx, LIB.lbm_profile_enable(ctx, 1 if on else 0))
+
+
+def lbm_profile_read(ctx):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(ctx, LIB.lbm_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def lbm_fluid_mask(ctx, mask):
+    return _check(ctx, LIB.lbm_fluid_mask(ctx, ptr(mask)))
+
+
+class Lattice:
+    """Owning handle of one context (single pipe or ensemble) with tensor conveniences."""
+
+    def __init__(self, grid, relax, force=None, stream=None, ensemble=None):
+        import torch
+        if stream is None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+        self._keep = [force]
+        if ensemble is not None:
+            grids, relaxes, forces = ensemble
+            self._keep.append(forces)
+            self.ctx = lbm_ensemble_create(grids, relaxes, forces, stream)
+            self.grids = list(grids)
+        else:
+            self.ctx = lbm_create(grid, relax, force, stream)
+            self.grids = [grid]
+        self.member = 0
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def grid(self):
+        return self.grids[self.member]
+
+    def select(self, m):
+        lbm_select_member(self.ctx, m)
+        self.member = m
+
+    def info(self):
+        return lbm_get_info(self.ctx)
+
+    def init(self, profile="rest", noise_amp=0.0, seed=0):
+        lbm_init(self.ctx, profile, noise_amp, seed)
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    def moments(self, device="cuda"):
+        import torch
+        g = self.grid
+        dt = torch.float64 if g.precision == LBM_F64 else torch.float32
+        rho = torch.empty((g.nz, g.ny, g.nx), dtype=dt, device=device)
+        u = torch.empty((3, g.nz, g.ny, g.nx), dtype=dt, device=device)
+        lbm_moments(self.ctx, rho, u)
+        return rho, u
+
+    def populations(self):
+        import numpy as np
+        g = self.grid
+        f = np.empty((27, g.nz, g.ny, g.nx), dtype=np.float64)
+        lbm_get_populations(self.ctx, f)
+        return f
+
+    def set_populations(self, f):
+        import numpy as np
+        lbm_set_populations(self.ctx, np.ascontiguousarray(f, dtype=np.float64))
+
+    def modes(self, n_sections=16, r_over_R=(0.78,), n_theta=None, n_modes=32):
+        import numpy as np
+        g = self.grid
+        if n_theta is None:
+            n_theta = 1 << max(3, math.ceil(math.log2(2 * math.pi * r_over_R[0] * g.R)))
+        cfg = make_modes_cfg(n_sections, r_over_R, n_theta, n_modes)
+        E = np.empty((n_sections, len(r_over_R), n_modes + 1))
+        lbm_modes(self.ctx, cfg, E)
+        return E

@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA step against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (derived from the arithmetic):
+* FP64 storage and collision: populations within 1e-12 of the oracle relative to
+  max|f| after 100 steps (each step adds O(1e-16) rounding differences from the
+  closed-form collision versus the literal 27x27 transforms).
+* FP32 shifted storage: velocity L2 error within 1e-5 relative after 1000 laminar
+  steps (float rounding of f - w ~ 1e-8 relative per step, accumulated).
+* FP16S / BF16 storage: the error statement of each format is measured and bounded
+  (11-bit and 8-bit significands).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from _pairs import TRIG_MODES, make_pair, perturbed_state, rel_err
+from oracle import lbm as O
+from oracle import modes as Mo
+from paper_2405_12082_gb300 import workloads as Wk
+
+pytestmark = pytest.mark.gpu
+
+
+def test_c1_laminar_pipe_fp64_fullway(lbm_lib):
+    """The plain-method configuration: 20x20x64, R = 8, full-way walls, g = 1e-6,
+    tau = 0.8, rest start: 1e-12 after 100 steps and after 500 steps."""
+    c = Wk.C1
+    L, ref = make_pair(lbm_lib, c["nx"], c["ny"], c["nz"], c["R"], precision="f64", wall="fullway",
+                       omega=c["omega"], g=c["g"])
+    L.init("rest")
+    ref.init("rest")
+    L.step(100)
+    ref.step(100)
+    assert rel_err(L.populations(), ref.f, ref.fluid) < 1e-12
+    L.step(400)
+    ref.step(400)
+    f = L.populations()
+    assert rel_err(f, ref.f, ref.fluid) < 1e-12
+    rho, u = L.moments()
+    rho_o, u_o = ref.moments()
+    m = ref.fluid
+    assert np.max(np.abs(u.cpu().numpy()[:, m] - u_o[:, m])) < 1e-12 * np.max(np.abs(u_o))
+    assert np.max(np.abs(rho.cpu().numpy()[m] - rho_o[m])) < 1e-13
+    L.close()
+
+
+@pytest.mark.parametrize("wall", ["halfway", "fullway", "bouzidi"])
+@pytest.mark.parametrize("steps", [1, 2, 3])
+def test_step_parity_from_nonequilibrium_state(lbm_lib, wall, steps):
+    """Both AA parities, every wall rule, a ragged 23x19x7 box (several blocks plus a tail)."""
+    L, ref = make_pair(lbm_lib, 23, 19, 7, 7.3, precision="f64", wall=wall, omega=1.7, g=(2e-5, -1e-5, 3e-5))
+    f0 = perturbed_state(ref, 101)
+    L.set_populations(f0)
+    back = L.populations()
+    assert rel_err(back, f0, ref.fluid) < 1e-16
+    L.step(steps)
+    ref.step(steps)
+    assert rel_err(L.populations(), ref.f, ref.fluid) < 1e-13
+    L.close()
+
+
+def test_trigger_and_field_force_parity(lbm_lib):
+    nz = 24
+    gz = Wk.gz_field(nz, 18, 18, base=2e-5, seed=Wk.SEED, rel_amp=0.5)
+    L, ref = make_pair(lbm_lib, 18, 18, nz, 7.5, precision="f64", wall="halfway", omega=1.5, g=(0, 0, 1e-5),
+                       trigger=dict(h=1e-4, period=30.0, modes=TRIG_MODES, t_end=9), gz=gz)
+    f0 = perturbed_state(ref, 202)
+    L.set_populations(f0)
+    for _ in range(4):
+        L.step(5)
+        ref.step(5)
+        assert rel_err(L.populations(), ref.f, ref.fluid) < 1e-12
+        rho, u = L.moments()
+        _, u_o = ref.moments()
+        m = ref.fluid
+        assert np.max(np.abs(u.cpu().numpy()[:, m] - u_o[:, m])) < 1e-12 * np.max(np.abs(u_o))
+    L.close()
+
+
+def test_periodic_box_taylor_green_parity(lbm_lib):
+    n = 24
+    k = 2 * math.pi / n
+    X, Y = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    u = np.zeros((3, 4, n, n))
+    u[0] = 0.02 * np.sin(k * X) * np.cos(k * Y)
+    u[1] = -0.02 * np.cos(k * X) * np.sin(k * Y)
+    u[2] = 0.01
+    L, ref = make_pair(lbm_lib, n, n, 4, 0.0, precision="f64", omega=1.1, g=(0, 0, 0), geometry="box")
+    ref.init_fields(np.ones((4, n, n)), u)
+    lbm_lib.lbm_init_fields(L.ctx, np.ones((4, n, n)), u)
+    assert rel_err(L.populations(), ref.f) < 1e-15
+    L.step(37)
+    ref.step(37)
+    assert rel_err(L.populations(), ref.f) < 1e-12
+    L.close()
+
+
+@pytest.mark.parametrize("profile", ["laminar", "loglaw"])
+def test_initial_state_parity(lbm_lib, profile):
+    """lbm_init: profile plus SplitMix64/Box-Muller noise against the oracle's own generator."""
+    L, ref = make_pair(lbm_lib, 20, 20, 10, 8.0, precision="f64", omega=1.9, g=(0, 0, 2e-5))
+    L.init(profile, noise_amp=1e-3, seed=99)
+    ref.init(profile, noise_amp=1e-3, seed=99)
+    assert rel_err(L.populations(), ref.f) < 1e-14
+    L.close()
+
+
+def test_raw_state_roundtrip_is_bit_exact(lbm_lib):
+    import torch
+    L, ref = make_pair(lbm_lib, 16, 16, 8, 6.0, precision="f32", omega=1.3)
+    L.init("laminar", noise_amp=1e-3, seed=5)
+    L.step(3)                                   # odd t: reversed layout
+    nbytes = L.info()["population_bytes"]
+    a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    lbm_lib.lbm_get_raw(L.ctx, a, nbytes)
+    L.step(4)
+    lbm_lib.lbm_set_raw(L.ctx, a, nbytes)
+    L2, _ = make_pair(lbm_lib, 16, 16, 8, 6.0, precision="f32", omega=1.3)
+    L2.init("laminar", noise_amp=1e-3, seed=5)
+    L2.step(3)
+    host = np.empty(nbytes, dtype=np.uint8)
+    lbm_lib.lbm_get_raw(L2.ctx, host, nbytes)
+    assert np.array_equal(a.cpu().numpy(), host)
+    L.close()
+    L2.close()
+
+
+def test_reduce_parity(lbm_lib):
+    L, ref = make_pair(lbm_lib, 21, 21, 9, 8.4, precision="f64", omega=1.6)
+    f0 = perturbed_state(ref, 303)
+    L.set_populations(f0)
+    L.step(3)
+    ref.step(3)
+    out = lbm_lib.lbm_reduce(L.ctx)
+    m = ref.fluid
+    from oracle.lattice import C
+    fo = ref.f[:, m]
+    assert abs(out[0] - (fo.sum() - m.sum())) < 1e-11
+    for a in range(3):
+        assert abs(out[1 + a] - np.sum(C[:, a][:, None] * fo)) < 1e-11
+    assert out[4] == 0
+    L.close()
+
+
+def test_stats_accumulators_parity(lbm_lib):
+    L, ref = make_pair(lbm_lib, 18, 18, 8, 7.0, precision="f64", omega=1.4, g=(0, 0, 1e-4))
+    f0 = perturbed_state(ref, 404)
+    L.set_populations(f0)
+    lbm_lib.lbm_stats_enable(L.ctx, 3)
+    ref.enable_stats(3)
+    L.step(11)
+    ref.step(11)
+    acc = np.empty((4, 8, 18, 18))
+    count = lbm_lib.lbm_stats_get(L.ctx, acc)
+    assert count == ref.stats_count == 4
+    for k in range(4):
+        scale = np.max(np.abs(ref.stats[k]))
+        assert np.max(np.abs(acc[k] - ref.stats[k])) < 1e-12 * scale
+    L.close()
+
+
+def test_modes_parity(lbm_lib):
+    """Ring analysis of Sec. II.C at 4 sections and 2 radii against the oracle's
+    correlation-based energies and dominant modes."""
+    nz = 16
+    L, ref = make_pair(lbm_lib, 40, 40, nz, 18.0, precision="f64", omega=1.5, g=(0, 0, 1e-5),
+                       trigger=dict(h=1e-4, period=30.0, modes=TRIG_MODES, t_end=100))
+    f0 = perturbed_state(ref, 505, u_amp=0.02)
+    L.set_populations(f0)
+    L.step(5)
+    ref.step(5)
+    E = L.modes(n_sections=4, r_over_R=(0.78, 0.5), n_theta=128, n_modes=20)
+    Eo = Mo.run_modes(ref, 4, (0.78, 0.5), 128, 20)
+    assert np.max(np.abs(E - Eo)) < 1e-10 * np.max(np.abs(Eo))
+    for s in range(4):
+        assert int(np.argmax(E[s, 0, 1:11])) + 1 == int(np.argmax(Eo[s, 0, 1:11])) + 1
+    L.close()
+
+
+def _laminar_pair(lbm_lib, precision, steps):
+    L, ref = make_pair(lbm_lib, 20, 20, 16, 8.0, precision=precision, wall="halfway", omega=1.25,
+                       g=(0, 0, 1e-5))
+    L.init("rest")
+    ref.init("rest")
+    L.step(steps)
+    ref.step(steps)
+    _, u = L.moments()
+    _, uo = ref.moments()
+    m = ref.fluid
+    d = u.double().cpu().numpy()[:, m] - uo[:, m]
+    L.close()
+    return float(np.sqrt(np.sum(d * d) / np.sum(uo[:, m] ** 2)))
+
+
+def test_fp32_velocity_error_after_1000_laminar_steps(lbm_lib):
+    err = _laminar_pair(lbm_lib, "f32", 1000)
+    assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("precision,bound", [("f16s", 2e-3), ("bf16", 2e-2)])
+def test_compressed_storage_error_statement(lbm_lib, precision, bound):
+    err = _laminar_pair(lbm_lib, precision, 1000)
+    assert err <= bound, err
+
+
+def test_degenerate_sizes(lbm_lib):
+    """n = 0 steps, a single-cell periodic box, nz = 1 pipes and a pipe with few fluid cells."""
+    L, ref = make_pair(lbm_lib, 1, 1, 1, 0.0, precision="f64", omega=1.2, g=(1e-4, 0, 0), geometry="box")
+    ref.init_fields(np.ones((1, 1, 1)), np.full((3, 1, 1, 1), 0.01))
+    L.set_populations(ref.f)
+    L.step(0)
+    L.step(5)
+    ref.step(5)
+    assert rel_err(L.populations(), ref.f) < 1e-14
+    L.close()
+    L, ref = make_pair(lbm_lib, 12, 12, 1, 5.0, precision="f64", wall="halfway", omega=1.2, g=(0, 0, 1e-4))
+    f0 = perturbed_state(ref, 606)
+    L.set_populations(f0)
+    L.step(7)
+    ref.step(7)
+    assert rel_err(L.populations(), ref.f, ref.fluid) < 1e-13
+    L.close()
+    L, ref = make_pair(lbm_lib, 6, 6, 5, 1.2, precision="f64", wall="bouzidi", omega=1.2, g=(0, 0, 1e-4))
+    f0 = perturbed_state(ref, 607)
+    L.set_populations(f0)
+    L.step(4)
+    ref.step(4)
+    assert rel_err(L.populations(), ref.f, ref.fluid) < 1e-13
+    L.close()
