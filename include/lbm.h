@@ -146,6 +146,8 @@ typedef struct {
  * (owned by the library, freed by lbm_free) and sets them to rest, f = w, t = 0.
  * stream: a cudaStream_t (NULL = legacy default stream) on which every later call
  * of this context runs.  Errors: LBM_EINVAL (bad grid, omega, force),
+ * LBM_EUNSUPPORTED (27 x cells of the context reach 2^32: the kernels index the
+ * population array with 32-bit element offsets, about 159 M cells at most),
  * LBM_ENOMEM, LBM_ECUDA.  *out is NULL on error. */
 int lbm_create(lbm_ctx **out, const lbm_grid *grid, const lbm_relax *relax,
                const lbm_force *force, void *stream);

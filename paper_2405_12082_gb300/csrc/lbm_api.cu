@@ -33,6 +33,7 @@ struct lbm_ctx {
     void *scratch = nullptr;         // staging for host buffers
     size_t scratch_bytes = 0;
     double *partials = nullptr;      // reduction partials + final (device)
+    void *geo = nullptr;             // column masks and trigger tables of every member (device)
     int64_t check_every = 0;
     double max_drift = 0;
     std::vector<double> mass0;
@@ -83,10 +84,48 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // fluid iff (2x - nx + 1)^2 + (2y - ny + 1)^2 < 4 R^2  <=>  ... <= ceil(4 R^2) - 1
 int64_t d2max_of(double R) { return (int64_t)std::ceil(4.0 * R * R) - 1; }
 
-bool col_fluid_host(const Member &d, int x, int y) {
-    if (d.geometry == LBM_BOX) return true;
-    int64_t X = 2 * (int64_t)x - d.nx + 1, Y = 2 * (int64_t)y - d.ny + 1;
-    return X * X + Y * Y <= d.d2max;
+bool col_fluid_host(const Member &d, int x, int y) { return lbm::col_fluid(d, x, y); }
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Device tables of every member: the 3x3 in-plane fluid mask of each column and the
+// trigger-force factors.  Allocated once; the force tables are refilled by set_force.
+int build_tables(lbm_ctx *c) {
+    const size_t es = c->precision == LBM_F64 ? 8 : 4;
+    std::vector<size_t> at(c->hm.size() * 3);
+    size_t total = 0;
+    for (size_t m = 0; m < c->hm.size(); ++m) {
+        const Member &d = c->hm[m];
+        const size_t ncol = (size_t)d.nx * d.ny;
+        at[3 * m] = total; total += align256(ncol * 2);
+        at[3 * m + 1] = total; total += align256(3 * ncol * es);
+        at[3 * m + 2] = total; total += align256(2 * (size_t)d.nz * es);
+    }
+    cudaError_t e = cudaMalloc(&c->geo, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->geo = nullptr;
+        return set_err(c, LBM_ENOMEM, "cannot allocate %zu bytes of geometry tables", total);
+    }
+    std::vector<uint16_t> mask;
+    for (size_t m = 0; m < c->hm.size(); ++m) {
+        Member &d = c->hm[m];
+        mask.assign((size_t)d.nx * d.ny, 0);
+        for (int y = 0; y < d.ny; ++y)
+            for (int x = 0; x < d.nx; ++x) {
+                uint16_t nb = 0;
+                for (int cy = -1; cy <= 1; ++cy)
+                    for (int cx = -1; cx <= 1; ++cx)
+                        if (col_fluid_host(d, x + cx, y + cy)) nb |= (uint16_t)(1u << lbm::nbit(cx, cy));
+                mask[(size_t)y * d.nx + x] = nb;
+            }
+        char *g = (char *)c->geo;
+        LBM_CUDA(c, cudaMemcpy(g + at[3 * m], mask.data(), mask.size() * 2, cudaMemcpyHostToDevice));
+        d.colmask = (const uint16_t *)(g + at[3 * m]);
+        d.ftab = g + at[3 * m + 1];
+        d.ztab = g + at[3 * m + 2];
+    }
+    return LBM_OK;
 }
 
 int check_force(lbm_ctx *c, const lbm_force *f) {
@@ -200,6 +239,8 @@ int upload_members(lbm_ctx *c) {
     return LBM_OK;
 }
 
+int fill_force_tables(lbm_ctx *c, int m);
+
 int ensure_scratch(lbm_ctx *c, size_t bytes) {
     if (bytes <= c->scratch_bytes) return LBM_OK;
     if (c->scratch) {
@@ -255,6 +296,11 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
         c->forces.push_back(force ? force[k] : fz);
     }
     if (blk >= (1ll << 31)) { delete c; return set_err(nullptr, LBM_EINVAL, "grid too large"); }
+    if (27 * off >= (1ll << 32)) {
+        delete c;
+        return set_err(nullptr, LBM_EUNSUPPORTED,
+                       "27 x %lld cells exceed the 32-bit population index of the step kernels", (long long)off);
+    }
     c->stride = off;
     c->nblocks = (int32_t)blk;
     c->esize = esize_of(prec);
@@ -279,7 +325,9 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
         lbm_free(c);
         return set_err(nullptr, LBM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     }
-    int rc = upload_members(c);
+    int rc = build_tables(c);
+    if (rc == LBM_OK) rc = upload_members(c);
+    for (size_t m = 0; rc == LBM_OK && m < c->hm.size(); ++m) rc = fill_force_tables(c, (int)m);
     if (rc) {
         g_create_error = c->err;
         lbm_free(c);
@@ -301,6 +349,15 @@ int dispatch(lbm_ctx *c, F &&f) {
     if (e != cudaSuccess) return cuda_err(c, e, "kernel launch");
     c->launches++;
     return LBM_OK;
+}
+
+int fill_force_tables(lbm_ctx *c, int m) {
+    const Member &d = c->hm[m];
+    if (!d.trig) return LBM_OK;
+    void *ft = const_cast<void *>(d.ftab), *zt = const_cast<void *>(d.ztab);
+    return dispatch(c, [&](auto P) {
+        return lbm::launch_force_tables<decltype(P)::value>(c->dm, d, m, ft, zt, c->stream);
+    });
 }
 
 int reduce_member(lbm_ctx *c, int m, double *host_out) {
@@ -371,6 +428,7 @@ void lbm_free(lbm_ctx *c) {
     cudaFree(c->stats);
     cudaFree(c->scratch);
     cudaFree(c->partials);
+    cudaFree(c->geo);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     cudaGetLastError();
     delete c;
@@ -421,7 +479,9 @@ int lbm_set_force(lbm_ctx *c, const lbm_force *f) {
     lbm_force fz;
     std::memset(&fz, 0, sizeof fz);
     c->forces[c->sel] = f ? *f : fz;
-    return upload_members(c);
+    rc = upload_members(c);
+    if (rc) return rc;
+    return fill_force_tables(c, c->sel);
 }
 
 int lbm_init(lbm_ctx *c, int32_t profile, double noise_amp, uint64_t seed) {

@@ -106,18 +106,21 @@ struct Member {
     int64_t t_end;
     const void *gz_field;
     uint32_t nx_mul, nx_shr, ny_mul, ny_shr;   // magic division by nx and ny
+    const uint16_t *colmask;   // [ny][nx] in-plane 3x3 fluid mask of every column (device)
+    const void *ftab;          // trigger: [3][ny][nx] column factors (P_x, P_y, P_z), compute type
+    const void *ztab;          // trigger: [2][nz] cos, sin of kz 2 pi z / L, compute type
 };
 
-// Unsigned division by a fixed divisor d >= 1 for n < 2^31: q = umulhi(n, mul) >> shr.
+// Unsigned division by a fixed divisor d >= 1 for n < 2^31 (Granlund-Montgomery with
+// a 31-bit dividend): l = ceil(log2 d), mul = ceil(2^(31+l) / d) < 2^32, and
+// n / d = umulhi(n, mul) >> (l - 1).  d = 1 is flagged by shr = 0xFFFFFFFF.
 inline void fastdiv_setup(uint32_t d, uint32_t &mul, uint32_t &shr) {
-    uint32_t s = 0;
-    while ((1ull << s) < d) ++s;
-    // mul = ceil(2^(32+s) / d); exact for n < 2^31 when d < 2^31
-    uint64_t m = ((1ull << (32 + s)) + d - 1) / d;
-    if (m >= (1ull << 32)) { // only for d == 1
-        mul = 0; shr = 0xFFFFFFFFu; return;
-    }
-    mul = (uint32_t)m; shr = s;
+    if (d <= 1) { mul = 0; shr = 0xFFFFFFFFu; return; }
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    const uint64_t m = ((1ull << (31 + l)) + d - 1) / d;
+    mul = (uint32_t)m;
+    shr = l - 1;
 }
 __device__ __forceinline__ uint32_t fastdiv(uint32_t n, uint32_t mul, uint32_t shr) {
     return shr == 0xFFFFFFFFu ? n : (__umulhi(n, mul) >> shr);
@@ -148,23 +151,24 @@ __device__ __forceinline__ int find_member(const StepArgs &a, int blk) {
 // ---- geometry --------------------------------------------------------------------------
 struct CellPos {
     int x, y, z;
-    int64_t cell;            // index inside the population plane (member offset added)
+    int32_t lc;              // cell index inside the member
     int32_t ox[3], oy[3], oz[3]; // neighbour offsets for c = -1, 0, +1 (periodic)
     uint32_t nb;             // in-plane fluid mask of the 3x3 neighbourhood
 };
 
-__device__ __forceinline__ bool col_fluid(const Member &d, int x, int y) {
+// Fluid test of a column (x, y) (pipe: distance to the axis < R, see lbm.h).
+__host__ __device__ __forceinline__ bool col_fluid(const Member &d, int x, int y) {
     if (d.geometry == LBM_BOX) return true;
-    int64_t X = 2 * (int64_t)x - d.nx + 1, Y = 2 * (int64_t)y - d.ny + 1;
+    const int64_t X = 2 * (int64_t)x - d.nx + 1, Y = 2 * (int64_t)y - d.ny + 1;
     return X * X + Y * Y <= d.d2max;
 }
 
 __device__ __forceinline__ void cell_setup(const Member &d, uint32_t local, CellPos &p) {
-    uint32_t q = fastdiv(local, d.nx_mul, d.nx_shr);
+    const uint32_t q = fastdiv(local, d.nx_mul, d.nx_shr);
     p.x = (int)(local - q * (uint32_t)d.nx);
     p.z = (int)fastdiv(q, d.ny_mul, d.ny_shr);
     p.y = (int)(q - (uint32_t)p.z * (uint32_t)d.ny);
-    p.cell = d.off + (int64_t)local;
+    p.lc = (int32_t)local;
     const int32_t nx = d.nx, nxy = d.nx * d.ny;
     p.ox[0] = p.x == 0 ? nx - 1 : -1;
     p.ox[1] = 0;
@@ -175,17 +179,7 @@ __device__ __forceinline__ void cell_setup(const Member &d, uint32_t local, Cell
     p.oz[0] = p.z == 0 ? (d.nz - 1) * nxy : -nxy;
     p.oz[1] = 0;
     p.oz[2] = p.z == d.nz - 1 ? -(d.nz - 1) * nxy : nxy;
-    uint32_t nb = 0;
-    if (d.geometry == LBM_BOX) {
-        nb = 0x1FF;
-    } else {
-#pragma unroll
-        for (int cy = -1; cy <= 1; ++cy)
-#pragma unroll
-            for (int cx = -1; cx <= 1; ++cx)
-                nb |= (uint32_t)col_fluid(d, p.x + cx, p.y + cy) << nbit(cx, cy);
-    }
-    p.nb = nb;
+    p.nb = d.colmask[(int32_t)(q - (uint32_t)p.z * (uint32_t)d.ny) * nx + p.x];
 }
 
 template <int I>
@@ -232,27 +226,32 @@ __device__ __forceinline__ BLink<R> bouzidi_link(const Member &d, const CellPos 
 
 // ---- loading and storing the 27 populations of a cell ------------------------------------
 // PAR 0: natural layout (after an odd step); PAR 1: reversed layout (after an even step).
+// Slot of direction i read at a cell: PAR 0 -> (i, x); PAR 1 -> (ibar, x - c_i), or (i, x)
+// across a wall link.  Slot written: PAR 0 -> (ibar, x); PAR 1 -> (i, x + c_i), or (ibar, x)
+// across a wall link.  Wall links choose the address with a select, not a branch.
+// Element indices are 32-bit: the library keeps 27 x stride below 2^32.
 template <int P, int PAR, int WALL>
 __device__ __forceinline__ void load_pops(const StepArgs &a, const Member &d, const CellPos &p,
                                           typename Storage<P>::R (&v)[Q]) {
     using S = Storage<P>;
     using T = typename S::T;
     using R = typename S::R;
-    const T *base = static_cast<const T *>(a.pops);
+    const T *base = static_cast<const T *>(a.pops) + d.off;
+    const uint32_t st = (uint32_t)a.stride;
+    const uint32_t lc = (uint32_t)p.lc;
     const R inv = (R)a.f16_inv;
     sfor<0, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int ib = opp_of(i);
         if constexpr (PAR == 0) {
-            v[i] = S::ld(base + (int64_t)i * a.stride + p.cell, inv);
+            v[i] = S::ld(base + (i * st + lc), inv);
         } else {
+            const uint32_t pull = ib * st + (uint32_t)(p.lc + src_offset<i>(p));
             if constexpr (WALL == LBM_FULLWAY || (cx_of(i) == 0 && cy_of(i) == 0)) {
-                v[i] = S::ld(base + (int64_t)ib * a.stride + p.cell + src_offset<i>(p), inv);
+                v[i] = S::ld(base + pull, inv);
             } else {
-                if (src_is_fluid<i>(p))
-                    v[i] = S::ld(base + (int64_t)ib * a.stride + p.cell + src_offset<i>(p), inv);
-                else
-                    v[i] = S::ld(base + (int64_t)i * a.stride + p.cell, inv);
+                const uint32_t own = i * st + lc;
+                v[i] = S::ld(base + (src_is_fluid<i>(p) ? pull : own), inv);
             }
         }
     });
@@ -277,13 +276,15 @@ __device__ __forceinline__ void store_pops(const StepArgs &a, const Member &d, c
     using S = Storage<P>;
     using T = typename S::T;
     using R = typename S::R;
-    T *base = static_cast<T *>(a.pops);
+    T *base = static_cast<T *>(a.pops) + d.off;
+    const uint32_t st = (uint32_t)a.stride;
+    const uint32_t lc = (uint32_t)p.lc;
     const R sc = (R)a.f16_scale;
-    // Bouzidi: the value reflected into slot Jbar becomes A f*_J + B f*_Jbar
-    R out[Q];
-    sfor<0, Q>([&](auto ic) { constexpr int i = decltype(ic)::value; out[i] = v[i]; });
     if constexpr (WALL == LBM_BOUZIDI) {
+        // the value reflected into slot Jbar becomes A f*_J + B f*_Jbar
         if (p.nb != 0x1FFu) {
+            R out[Q];
+            sfor<0, Q>([&](auto ic) { constexpr int i = decltype(ic)::value; out[i] = v[i]; });
             sfor<0, Q>([&](auto jc) {
                 constexpr int j = decltype(jc)::value;
                 if constexpr (cx_of(j) != 0 || cy_of(j) != 0) {
@@ -293,80 +294,82 @@ __device__ __forceinline__ void store_pops(const StepArgs &a, const Member &d, c
                     }
                 }
             });
+            sfor<0, Q>([&](auto ic) { constexpr int i = decltype(ic)::value; v[i] = out[i]; });
         }
     }
     sfor<0, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int ib = opp_of(i);
         if constexpr (PAR == 0) {
-            S::st(base + (int64_t)ib * a.stride + p.cell, out[i], sc);
+            S::st(base + (ib * st + lc), v[i], sc);
         } else {
+            const uint32_t push = i * st + (uint32_t)(p.lc + nb_offset<i>(p));
             if constexpr (WALL == LBM_FULLWAY || (cx_of(i) == 0 && cy_of(i) == 0)) {
-                S::st(base + (int64_t)i * a.stride + p.cell + nb_offset<i>(p), out[i], sc);
+                S::st(base + push, v[i], sc);
             } else {
-                if (dst_is_fluid<i>(p))
-                    S::st(base + (int64_t)i * a.stride + p.cell + nb_offset<i>(p), out[i], sc);
-                else
-                    S::st(base + (int64_t)ib * a.stride + p.cell, out[i], sc);
+                const uint32_t own = ib * st + lc;
+                S::st(base + (dst_is_fluid<i>(p) ? push : own), v[i], sc);
             }
         }
     });
 }
 
 // ---- acceleration g(x, t), Sec. II.B ----------------------------------------------------------
+// The trigger force of Eq. (TurbForce) factorises into st(t) x z-factor x column factor:
+// g_x = st cos(2 pi kz z / L) P_x(x, y), g_y = st cos(...) P_y(x, y),
+// g_z = st sin(2 pi kz z / L) P_z(x, y); the column factors (zero outside the radial
+// band) and the z factors are tabulated once per force by k_force_tables.
 template <class R>
 __device__ __forceinline__ void acceleration(const Member &d, const CellPos &p, int64_t t, double st,
                                              R &gx, R &gy, R &gz) {
     gx = (R)d.g[0];
     gy = (R)d.g[1];
     gz = (R)d.g[2];
-    if (d.gz_field != nullptr) {
-        const int64_t local = p.cell - d.off;
-        gz += (R)(static_cast<const R *>(d.gz_field)[local]);
+    if (d.gz_field != nullptr) gz += static_cast<const R *>(d.gz_field)[p.lc];
+    if (d.trig && t < d.t_end) {
+        const R *ft = static_cast<const R *>(d.ftab);
+        const R *zt = static_cast<const R *>(d.ztab);
+        const int32_t col = p.y * d.nx + p.x, ncol = d.nx * d.ny;
+        const R s = (R)st;
+        const R sc = s * zt[p.z], ss = s * zt[d.nz + p.z];
+        gx += sc * ft[col];
+        gy += sc * ft[ncol + col];
+        gz += ss * ft[2 * ncol + col];
     }
-    if (d.trig && t < d.t_end && d.geometry == LBM_PIPE) {
-        const R px = R(0.5) * R(2 * p.x - d.nx + 1), py = R(0.5) * R(2 * p.y - d.ny + 1);
-        const R r = sqrt(px * px + py * py);
-        const R Rr = (R)d.R, l0 = (R)d.l0, l = (R)d.l;
-        if (r >= Rr - l0 - l && r <= Rr - l0 && r > R(0)) {
-            const R ir = R(1) / r;
-            const R ct = px * ir, sn = py * ir;
-            const R L = (R)d.nz;
-            R sa, ca, sz, cz;
-            sincospi(R(2) * (Rr - r - l0) / l, &sa, &ca);
-            sincospi(R(2) * R(d.kz) * R(p.z) / L, &sz, &cz);
-            const R s = (R)st;
-            const R kap = (R)d.kappa;
-            const R twopi = R(6.283185307179586476925286766559);
-            R Fr = 0, Ft = 0, Fz = 0;
-            // cos(k theta), sin(k theta) by repeated multiplication with e^{i theta}
-            R ck = 1, sk = 0;
-            int k = 0;
-            for (int q = 0; q < d.n_modes; ++q) {
-                const int kt = d.k_theta[q];
-                while (k < kt) {
-                    const R c2 = ck * ct - sk * sn;
-                    sk = sk * ct + ck * sn;
-                    ck = c2;
-                    ++k;
-                }
-                if (k > kt) {   // modes given out of order: restart
-                    ck = 1; sk = 0; k = 0;
-                    while (k < kt) { const R c2 = ck * ct - sk * sn; sk = sk * ct + ck * sn; ck = c2; ++k; }
-                }
-                const R cph = (R)d.cph[q], sph = (R)d.sph[q];
-                const R cang = ck * cph - sk * sph;
-                const R sang = sk * cph + ck * sph;
-                const R A = (R)d.amp[q] * s;
-                Fr -= A * kap * (Rr * ir) * (R(d.kz) * l / L) * (R(1) - ca) * cz * cang;
-                Ft += A * (R(1) - kap) * (R(d.kz) / R(kt)) * (twopi * Rr / L) * sa * cz * sang;
-                Fz -= A * (Rr * ir) * sa * sz * cang;
-            }
-            gx += Fr * ct - Ft * sn;
-            gy += Fr * sn + Ft * ct;
-            gz += Fz;
+}
+
+// Column and z factors of the trigger force (see acceleration), in double.
+__device__ __forceinline__ void trigger_column(const Member &d, int x, int y, double &Px, double &Py, double &Pz) {
+    Px = Py = Pz = 0.0;
+    if (d.geometry != LBM_PIPE || !d.trig) return;
+    const double px = 0.5 * (double)(2 * x - d.nx + 1), py = 0.5 * (double)(2 * y - d.ny + 1);
+    const double r = sqrt(px * px + py * py);
+    const double R = d.R, l0 = d.l0, l = d.l, L = (double)d.nz;
+    if (!(r >= R - l0 - l && r <= R - l0 && r > 0.0)) return;
+    const double ir = 1.0 / r, ct = px * ir, sn = py * ir;
+    double sa, ca;
+    sincospi(2.0 * (R - r - l0) / l, &sa, &ca);
+    const double kz = (double)d.kz, kap = d.kappa;
+    const double twopi = 6.283185307179586476925286766559;
+    double Ar = 0, At = 0, Az = 0;
+    for (int q = 0; q < d.n_modes; ++q) {
+        const int kt = d.k_theta[q];
+        double ck = 1, sk = 0;           // cos, sin of kt theta by repeated rotation
+        for (int k = 0; k < kt; ++k) {
+            const double c2 = ck * ct - sk * sn;
+            sk = sk * ct + ck * sn;
+            ck = c2;
         }
+        const double cang = ck * d.cph[q] - sk * d.sph[q];
+        const double sang = sk * d.cph[q] + ck * d.sph[q];
+        const double A = d.amp[q];
+        Ar += A * kap * (R * ir) * (kz * l / L) * (1.0 - ca) * cang;   // F_r = -st cz Ar
+        At += A * (1.0 - kap) * (kz / kt) * (twopi * R / L) * sa * sang; // F_t =  st cz At
+        Az += A * (R * ir) * sa * cang;                                 // F_z = -st sz Az
     }
+    Px = -Ar * ct - At * sn;
+    Py = -Ar * sn + At * ct;
+    Pz = -Az;
 }
 
 // ---- collision ------------------------------------------------------------------------------

@@ -40,7 +40,15 @@ template <int P>
 cudaError_t launch_modes(int wall, int parity, const StepArgs &a, const Member &hm, int m,
                          const ModesArgs &ma, double *E, cudaStream_t s);
 
-constexpr int STEP_BLOCK_HOST = 256;   // threads per block of the step kernel
+// Trigger-force tables of member m (column factors [3][ny][nx], z factors [2][nz]).
+template <int P>
+cudaError_t launch_force_tables(const Member *dmembers, const Member &hm, int m, void *ftab, void *ztab,
+                                cudaStream_t s);
+
+#ifndef LBM_STEP_BLOCK
+#define LBM_STEP_BLOCK 256
+#endif
+constexpr int STEP_BLOCK_HOST = LBM_STEP_BLOCK;   // threads per block of the step kernel
 constexpr int REDUCE_BLOCK = 256;
 constexpr int REDUCE_MAX_BLOCKS = 1216;   // 8 resident blocks x 152 SMs
 

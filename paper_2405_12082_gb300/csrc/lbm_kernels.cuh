@@ -3,17 +3,23 @@
 // LBM_PREC before including this file).
 #pragma once
 
+#include <algorithm>
+
 #include "lbm_internal.h"
 
 namespace lbm {
 
 constexpr int STEP_BLOCK = STEP_BLOCK_HOST;
+#ifndef LBM_STEP_MIN_BLOCKS
+#define LBM_STEP_MIN_BLOCKS 4
+#endif
+constexpr int STEP_MIN_BLOCKS = LBM_STEP_MIN_BLOCKS;   // resident blocks per SM the registers must allow
 
 // ---- the fused step: load (stream) + wall + force + MRT collision + store ----------------
 // One thread per cell of every member; solid cells return at once.  On sample
 // steps (STATS) u_z^k, k = 1..4, of the pre-collision state is added in FP64.
 template <int P, int PAR, int WALL, bool STATS>
-__global__ void __launch_bounds__(STEP_BLOCK) k_step(const __grid_constant__ StepArgs a) {
+__global__ void __launch_bounds__(STEP_BLOCK, STEP_MIN_BLOCKS) k_step(const __grid_constant__ StepArgs a) {
     using R = typename Storage<P>::R;
     const int m = find_member(a, blockIdx.x);
     const Member &d = a.members[m];
@@ -29,7 +35,7 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_step(const __grid_constant__ Ste
     const Macro<R> mm = collide<R>(v, gx, gy, gz, (R)d.omega);
     if constexpr (STATS) {
         const double uz = (double)mm.uz;
-        double *s = a.stats + p.cell;
+        double *s = a.stats + d.off + p.lc;
         const double uz2 = uz * uz;
         s[0] += uz;
         s[a.stride] += uz2;
@@ -61,19 +67,21 @@ __device__ __forceinline__ void write_state(const StepArgs &a, const Member &d, 
             });
         }
     }
+    T *b = base + d.off;
+    const uint32_t st = (uint32_t)a.stride;
+    const uint32_t lc = (uint32_t)p.lc;
     sfor<0, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int ib = opp_of(i);
         if constexpr (PAR == 0) {
-            S::st(base + (int64_t)i * a.stride + p.cell, v[i], sc);
+            S::st(b + (i * st + lc), v[i], sc);
         } else {
+            const uint32_t pull = ib * st + (uint32_t)(p.lc + src_offset<i>(p));
             if constexpr (WALL == LBM_FULLWAY || (cx_of(i) == 0 && cy_of(i) == 0)) {
-                S::st(base + (int64_t)ib * a.stride + p.cell + src_offset<i>(p), v[i], sc);
+                S::st(b + pull, v[i], sc);
             } else {
-                if (src_is_fluid<i>(p))
-                    S::st(base + (int64_t)ib * a.stride + p.cell + src_offset<i>(p), v[i], sc);
-                else
-                    S::st(base + (int64_t)i * a.stride + p.cell, v[i], sc);
+                const uint32_t own = i * st + lc;
+                S::st(b + (src_is_fluid<i>(p) ? pull : own), v[i], sc);
             }
         }
     });
@@ -351,6 +359,27 @@ __global__ void k_modes(const __grid_constant__ StepArgs a, int m, const ModesAr
     }
 }
 
+// ---- trigger-force tables ---------------------------------------------------------------------
+template <class R>
+__global__ void k_force_tables(const Member *members, int m, R *ftab, R *ztab) {
+    const Member &d = members[m];
+    const int ncol = d.nx * d.ny;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < ncol) {
+        double Px, Py, Pz;
+        trigger_column(d, k % d.nx, k / d.nx, Px, Py, Pz);
+        ftab[k] = (R)Px;
+        ftab[ncol + k] = (R)Py;
+        ftab[2 * ncol + k] = (R)Pz;
+    }
+    if (k < d.nz) {
+        double sz, cz;
+        sincospi(2.0 * (double)d.kz * (double)k / (double)d.nz, &sz, &cz);
+        ztab[k] = (R)cz;
+        ztab[d.nz + k] = (R)sz;
+    }
+}
+
 // ---- host launchers ------------------------------------------------------------------------------
 #define LBM_DISPATCH_WP(WALL_, PAR_, ...)                                          \
     do {                                                                          \
@@ -431,6 +460,15 @@ cudaError_t launch_reduce(int wall, int parity, const StepArgs &a, const Member 
 }
 
 template <int P>
+cudaError_t launch_force_tables(const Member *dmembers, const Member &hm, int m, void *ftab, void *ztab,
+                                cudaStream_t s) {
+    using R = typename Storage<P>::R;
+    const int n = (int)std::max<int64_t>((int64_t)hm.nx * hm.ny, hm.nz);
+    k_force_tables<R><<<blocks_for(n, 256), 256, 0, s>>>(dmembers, m, (R *)ftab, (R *)ztab);
+    return cudaGetLastError();
+}
+
+template <int P>
 cudaError_t launch_modes(int wall, int parity, const StepArgs &a, const Member &hm, int m, const ModesArgs &ma,
                          double *E, cudaStream_t s) {
     (void)hm;
@@ -464,4 +502,6 @@ cudaError_t launch_modes(int wall, int parity, const StepArgs &a, const Member &
                                           int, double *, cudaStream_t);                                 \
     template cudaError_t launch_modes<P>(int, int, const StepArgs &, const Member &, int,               \
                                          const ModesArgs &, double *, cudaStream_t);                    \
+    template cudaError_t launch_force_tables<P>(const Member *, const Member &, int, void *, void *,     \
+                                                cudaStream_t);                                          \
     }
