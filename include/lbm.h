@@ -272,6 +272,38 @@ int lbm_profile_read(lbm_ctx *ctx, double *ms, int64_t *launches);
  * selected member, exactly as the kernels decide it.  Host memory. */
 int lbm_fluid_mask(lbm_ctx *ctx, uint8_t *mask);
 
+/* ==== reduction without allocation ====================================================== */
+
+/* The paper has no counterpart to this call; it serves callers that may not allocate
+ * device memory at the moment they need the sum -- an application whose device memory
+ * belongs wholly to its own pool, or a latency-critical loop that cannot afford the
+ * device-wide synchronisation of cudaMalloc/cudaFree.  It computes what lbm_reduce
+ * computes, from a population array the caller passes in, and allocates nothing.
+ *
+ * pops: device array [27][n_cells] in the storage precision `precision`, holding
+ *       f_i - w_i (scaled by 2^f16_log2_scale for LBM_F16S; 0 selects 16) in the
+ *       natural layout of an even time step, e.g. a copy made by lbm_get_raw at even t.
+ * out:  device memory for 5 doubles: sum (f - w), the three momentum sums
+ *       sum c_i (f_i - w_i) and the number of cells with a non-finite value.  For a
+ *       context with half-way walls at even t, whose solid and padding slots hold
+ *       zero, this equals lbm_reduce of that context.
+ * The block partials live in a fixed static device array of
+ * LBM_STATIC_REDUCE_MAX_BLOCKS x 5 + 8 doubles (48,704 bytes) that every GPU loading
+ * the library keeps until the process exits.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  All calls on a device share the array
+ * and each overwrites what it reads, so nothing needs clearing, but calls whose
+ * kernels overlap on the GPU race: order them (one stream).  Asynchronous on
+ * `stream` (a cudaStream_t, NULL = default stream).
+ * Errors: LBM_EINVAL (NULL pointer, n_cells < 1 or above LBM_STATIC_REDUCE_MAX_CELLS,
+ * unknown precision or scale, out not device memory), LBM_ECUDA (no current device,
+ * symbol lookup or launch failure).  Calls no cudaMalloc, cudaFree or other
+ * allocating routine. */
+#define LBM_STATIC_REDUCE_MAX_BLOCKS 1216
+#define LBM_STATIC_REDUCE_MAX_CELLS  159072862   /* floor((2^32 - 1) / 27) */
+int lbm_reduce_static(const void *pops, int32_t precision, int32_t f16_log2_scale, int64_t n_cells,
+                      double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

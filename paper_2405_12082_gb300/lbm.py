@@ -23,6 +23,8 @@ LBM_REST, LBM_LAMINAR, LBM_LOGLAW = 0, 1, 2
 LBM_J_UBULK, LBM_J_WSS = 0, 1
 LBM_MAX_TRIGGER_MODES = 8
 LBM_MAX_MEMBERS = 64
+LBM_STATIC_REDUCE_MAX_BLOCKS = 1216
+LBM_STATIC_REDUCE_MAX_CELLS = 159072862
 
 PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16": LBM_BF16}
 WALLS = {"halfway": LBM_HALFWAY, "fullway": LBM_FULLWAY, "bouzidi": LBM_BOUZIDI}
@@ -99,6 +101,7 @@ def _load():
         "lbm_profile_enable": [P, I32],
         "lbm_profile_read": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
         "lbm_fluid_mask": [P, P],
+        "lbm_reduce_static": [P, I32, I32, I64, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -117,7 +120,7 @@ EXPORTED = ("lbm_create", "lbm_ensemble_create", "lbm_free", "lbm_last_error", "
             "lbm_init_fields", "lbm_step", "lbm_set_check", "lbm_moments", "lbm_get_populations",
             "lbm_set_populations", "lbm_get_raw", "lbm_set_raw", "lbm_reduce", "lbm_stats_enable",
             "lbm_stats_get", "lbm_modes", "lbm_adjoint", "lbm_profile_enable", "lbm_profile_read",
-            "lbm_fluid_mask")
+            "lbm_fluid_mask", "lbm_reduce_static")
 
 
 # ---- marshalling helpers -----------------------------------------------------------------
@@ -315,6 +318,15 @@ def lbm_profile_read(ctx):
 
 def lbm_fluid_mask(ctx, mask):
     return _check(ctx, LIB.lbm_fluid_mask(ctx, ptr(mask)))
+
+
+def lbm_reduce_static(pops, precision, f16_log2_scale, n_cells, out, stream=None):
+    """Allocation-free reduction (see include/lbm.h); out is a device buffer of 5 doubles."""
+    precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+    rc = LIB.lbm_reduce_static(ptr(pops), int(precision), int(f16_log2_scale), int(n_cells), ptr(out), ptr(stream))
+    if rc != LBM_OK:
+        raise LbmError(rc, "lbm_reduce_static rejected its arguments or failed to launch")
+    return rc
 
 
 class Lattice:
