@@ -40,7 +40,9 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="c2", choices=["c2", "c3"])
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"])
+    p.add_argument("--graph", type=int, default=None, help="steps per captured graph (0 = direct launches)")
+    p.add_argument("--autotune", action="store_true", help="pick the step-kernel launch shape by timing")
     p.add_argument("--precision", default="f32", choices=["f32", "f16s", "bf16", "f64"])
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -48,27 +50,47 @@ def parse():
 
 
 def workload(name):
-    return dict(Wk.C2 if name == "c2" else Wk.C3)
+    return dict({"c2": Wk.C2, "c3": Wk.C3, "c4": Wk.C4}[name])
 
 
-def config_json(cfg, args, n_gpus):
-    return {"workload": cfg["name"], "grid": [cfg["nx"], cfg["ny"], cfg["nz"]], "R": cfg["R"],
-            "precision": args.precision, "wall": "halfway", "lbm_steps_per_step": LBM_STEPS_PER_STEP,
-            "stats_every": cfg["stats_every"], "mode_sections": cfg["n_sections"], "n_theta": cfg["n_theta"],
-            "trigger_modes": [m[0] for m in cfg["trigger_modes"]],
-            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas x%d" % n_gpus}
+def config_json(cfg, args, n_gpus, graph=0, tuned=None):
+    out = {"workload": cfg["name"], "precision": args.precision, "wall": "halfway",
+           "lbm_steps_per_step": LBM_STEPS_PER_STEP, "l2": "inputs larger than L2 (no flush)",
+           "parallelism": "replicas x%d" % n_gpus, "graph_chunk": graph}
+    if tuned is not None:
+        out["launch_shape"] = {"variant": tuned[0], "us_per_step": tuned[1]}
+    if args.workload == "c4":
+        mem = Wk.ensemble_members(Wk.SEED, cfg["n"], cfg["radii"], cfg["u_star"])
+        out.update({"members": cfg["n"], "radii": [m["R"] for m in mem], "nz": cfg["nz"],
+                    "trigger_modes": [2]})
+    else:
+        out.update({"grid": [cfg["nx"], cfg["ny"], cfg["nz"]], "R": cfg["R"],
+                    "stats_every": cfg["stats_every"], "mode_sections": cfg["n_sections"],
+                    "n_theta": cfg["n_theta"], "trigger_modes": [m[0] for m in cfg["trigger_modes"]]})
+    return out
 
 
 # ---------------------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline): a bounded z-slab sample of the same pipe
 # ---------------------------------------------------------------------------------------
-def _oracle_sample(cfg, nz_sample, min_seconds, max_steps, out_q=None):
+def oracle_pipe(cfg):
+    """The single pipe the oracle samples: the workload's pipe, or member 0 of the ensemble."""
+    if "nx" in cfg:
+        return dict(nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], R=cfg["R"], omega=cfg["omega"], h=cfg["h"],
+                    period=cfg["period"], modes=cfg["trigger_modes"], t_end=cfg["t_trigger"], noise=cfg["noise"])
+    mem = Wk.ensemble_members(Wk.SEED, cfg["n"], cfg["radii"], cfg["u_star"])[0]
+    n = Wk.box_side(mem["R"])
+    return dict(nx=n, ny=n, nz=cfg["nz"], R=mem["R"], omega=cfg["omega"], h=mem["h"], period=mem["period"],
+                modes=[(2, 1.0, mem["phase"])], t_end=mem["t_end"], noise=Wk.C2["noise"])
+
+
+def _oracle_sample(cfg, nz_sample, min_seconds, max_steps):
     from oracle import lbm as O
-    tr = O.Trigger(h=cfg["h"], R=cfg["R"], L=cfg["nz"], period=cfg["period"], modes=cfg["trigger_modes"],
-                   t_end=cfg["t_trigger"])
-    run = O.Run(cfg["nx"], cfg["ny"], nz_sample, omega=cfg["omega"], R=cfg["R"], wall="halfway",
-                g=(0.0, 0.0, cfg["h"]), trigger=tr)
-    run.init("loglaw", cfg["noise"], Wk.SEED)
+    pp = oracle_pipe(cfg)
+    tr = O.Trigger(h=pp["h"], R=pp["R"], L=pp["nz"], period=pp["period"], modes=pp["modes"], t_end=pp["t_end"])
+    run = O.Run(pp["nx"], pp["ny"], nz_sample, omega=pp["omega"], R=pp["R"], wall="halfway",
+                g=(0.0, 0.0, pp["h"]), trigger=tr)
+    run.init("loglaw", pp["noise"], Wk.SEED)
     n_fluid = int(run.fluid.sum())
     steps = 0
     t0 = time.perf_counter()
@@ -78,7 +100,8 @@ def _oracle_sample(cfg, nz_sample, min_seconds, max_steps, out_q=None):
         if min_seconds > 0 and steps >= 2 and time.perf_counter() - t0 >= min_seconds:
             break
     dt = time.perf_counter() - t0
-    return {"updates": n_fluid * steps, "seconds": dt, "steps": steps, "n_fluid": n_fluid}
+    return {"updates": n_fluid * steps, "seconds": dt, "steps": steps, "n_fluid": n_fluid,
+            "shape": [pp["nx"], pp["ny"], nz_sample]}
 
 
 def oracle_in_child(cfg_name, nz_sample, min_seconds, max_steps):
@@ -100,7 +123,7 @@ def cpu_baseline(args, cfg):
     val = res["updates"] / res["seconds"] / 1e6
     return {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": "FP64 numpy oracle, %d steps of a %dx%dx%d z-slab of the same pipe (%d fluid cells), "
-                      "one thread" % (res["steps"], cfg["nx"], cfg["ny"], nz_sample, res["n_fluid"])}
+                      "one thread" % ((res["steps"],) + tuple(res["shape"]) + (res["n_fluid"],))}
 
 
 def run_reference(args):
@@ -119,7 +142,7 @@ def run_reference(args):
             "data": "synthetic", "config": config_json(cfg, args, 1),
             "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                              "sample": "%d oracle steps of a %dx%dx%d z-slab per run" % (
-                                 res["steps"], cfg["nx"], cfg["ny"], nz_sample)},
+                                 (res["steps"],) + tuple(res["shape"]))},
             "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -196,6 +219,33 @@ def profiled_traffic(precision, workload_name):
     return None
 
 
+def build_single(lbm, cfg, args, stream, rank):
+    grid = lbm.make_grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["R"], precision=args.precision, wall="halfway")
+    trig = Wk.trigger_dict(h=cfg["h"], R=cfg["R"], nz=cfg["nz"], period=cfg["period"],
+                           modes=cfg["trigger_modes"], t_end=cfg["t_trigger"])
+    force = lbm.make_force(g=(0.0, 0.0, cfg["h"]), trigger=trig)
+    L = lbm.Lattice(grid, lbm.lbm_relax(cfg["omega"]), force, stream=stream.cuda_stream)
+    L.init("loglaw", noise_amp=cfg["noise"], seed=Wk.SEED + rank)
+    lbm.lbm_stats_enable(L.ctx, cfg["stats_every"])
+    return L
+
+
+def build_ensemble(lbm, cfg, args, stream, rank):
+    members = Wk.ensemble_members(Wk.SEED, cfg["n"], cfg["radii"], cfg["u_star"])
+    grids, relaxes, forces = [], [], []
+    for mem in members:
+        R = mem["R"]
+        n = Wk.box_side(R)
+        grids.append(lbm.make_grid(n, n, cfg["nz"], R, precision=args.precision, wall="halfway"))
+        relaxes.append(lbm.lbm_relax(cfg["omega"]))
+        trig = Wk.trigger_dict(h=mem["h"], R=R, nz=cfg["nz"], period=mem["period"], modes=[(2, 1.0, mem["phase"])],
+                               t_end=mem["t_end"])
+        forces.append(lbm.make_force(g=(0.0, 0.0, mem["h"]), trigger=trig))
+    L = lbm.Lattice(None, None, stream=stream.cuda_stream, ensemble=(grids, relaxes, forces))
+    L.init("loglaw", noise_amp=cfg["noise"], seed=Wk.SEED + 1000 * rank)
+    return L
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -209,28 +259,39 @@ def run_ours(args):
     torch.cuda.set_device(local)
 
     cfg = workload(args.workload)
+    ensemble = args.workload == "c4"
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, cfg)     # host-only child process, before heavy GPU use
 
     from paper_2405_12082_gb300 import lbm
     stream = torch.cuda.current_stream()
-    grid = lbm.make_grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["R"], precision=args.precision, wall="halfway")
-    trig = Wk.trigger_dict(h=cfg["h"], R=cfg["R"], nz=cfg["nz"], period=cfg["period"],
-                           modes=cfg["trigger_modes"], t_end=cfg["t_trigger"])
-    force = lbm.make_force(g=(0.0, 0.0, cfg["h"]), trigger=trig)
-    L = lbm.Lattice(grid, lbm.lbm_relax(cfg["omega"]), force, stream=stream.cuda_stream)
-    L.init("loglaw", noise_amp=cfg["noise"], seed=Wk.SEED + rank)
-    lbm.lbm_stats_enable(L.ctx, cfg["stats_every"])
+    L = (build_ensemble if ensemble else build_single)(lbm, cfg, args, stream, rank)
     info = L.info()
-    n_fluid = info["n_fluid"]
-    mcfg = lbm.make_modes_cfg(cfg["n_sections"], cfg["r_over_R"], cfg["n_theta"], cfg["n_modes"])
-    E = torch.empty((cfg["n_sections"], len(cfg["r_over_R"]), cfg["n_modes"] + 1), dtype=torch.float64,
-                    device="cuda")
+    n_members = info["n_members"]
+    n_fluid = 0
+    cells = []
+    for m in range(n_members):
+        L.select(m)
+        mi = L.info()
+        n_fluid += mi["n_fluid"]
+        cells.append(mi["n_cells"])
+    L.select(0)
+    tuned = None
+    if args.autotune or ensemble:
+        tuned = lbm.lbm_autotune(L.ctx, 20)
+    graph = args.graph if args.graph is not None else (LBM_STEPS_PER_STEP if ensemble else 0)
+    if graph:
+        lbm.lbm_set_graph(L.ctx, graph)
+    if not ensemble:
+        mcfg = lbm.make_modes_cfg(cfg["n_sections"], cfg["r_over_R"], cfg["n_theta"], cfg["n_modes"])
+        E = torch.empty((cfg["n_sections"], len(cfg["r_over_R"]), cfg["n_modes"] + 1), dtype=torch.float64,
+                        device="cuda")
 
     def one_step():
         lbm.lbm_step(L.ctx, LBM_STEPS_PER_STEP)
-        lbm.lbm_modes(L.ctx, mcfg, E)
+        if not ensemble:
+            lbm.lbm_modes(L.ctx, mcfg, E)
 
     for _ in range(args.warmup):
         one_step()
@@ -263,30 +324,37 @@ def run_ours(args):
     value = updates / (ms * 1e-3) / 1e6
 
     # end to end through the C ABI with host buffers: upload the state from pinned host
-    # memory, advance one bench step, read the mode energies and the velocity field back
+    # memory, advance one bench step, read the results back to host memory (ring energies
+    # and the velocity field; for the ensemble every member's velocity field)
     nbytes = info["population_bytes"]
     host_state = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     lbm.lbm_get_raw(L.ctx, host_state, nbytes)
-    cells = info["n_cells"]
-    dt_np = np.float64 if args.precision == "f64" else np.float32
-    rho_h = torch.empty(cells, dtype=torch.float64 if args.precision == "f64" else torch.float32,
-                        pin_memory=True)
-    u_h = torch.empty(3 * cells, dtype=rho_h.dtype, pin_memory=True)
-    E_h = np.empty((cfg["n_sections"], len(cfg["r_over_R"]), cfg["n_modes"] + 1))
+    fdt = torch.float64 if args.precision == "f64" else torch.float32
+    rho_h = [torch.empty(c, dtype=fdt, pin_memory=True) for c in cells]
+    u_h = [torch.empty(3 * c, dtype=fdt, pin_memory=True) for c in cells]
+    E_h = None if ensemble else np.empty((cfg["n_sections"], len(cfg["r_over_R"]), cfg["n_modes"] + 1))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         lbm.lbm_set_raw(L.ctx, host_state, nbytes)
         lbm.lbm_step(L.ctx, LBM_STEPS_PER_STEP)
-        lbm.lbm_modes(L.ctx, mcfg, E_h)
-        lbm.lbm_moments(L.ctx, rho_h, u_h)
+        if not ensemble:
+            lbm.lbm_modes(L.ctx, mcfg, E_h)
+        for m in range(n_members):
+            L.select(m)
+            lbm.lbm_moments(L.ctx, rho_h[m], u_h[m])
+        L.select(0)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_val = n_fluid * LBM_STEPS_PER_STEP * args.e2e_steps * world / e2e_s / 1e6
-    d2h = E_h.nbytes + rho_h.numel() * rho_h.element_size() + u_h.numel() * u_h.element_size()
+    e2e_val = n_fluid * LBM_STEPS_PER_STEP * max(args.e2e_steps, 1) * world / max(e2e_s, 1e-9) / 1e6
+    d2h = sum(r.numel() * r.element_size() + u.numel() * u.element_size() for r, u in zip(rho_h, u_h))
+    if E_h is not None:
+        d2h += E_h.nbytes
 
-    # health of the run: finite populations after everything above
-    red = lbm.lbm_reduce(L.ctx)
+    bad = 0.0
+    for m in range(n_members):
+        L.select(m)
+        bad += lbm.lbm_reduce(L.ctx)[4]
     L.close()
     if world > 1:
         dist.barrier()
@@ -304,7 +372,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "f32",
         "storage": args.precision, "data": "synthetic (seeded log-law + noise, paper-shaped pipe)",
-        "config": config_json(cfg, args, world),
+        "config": config_json(cfg, args, world, graph, tuned),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None,
                      "traffic": profiled_traffic(args.precision, args.workload),
@@ -315,7 +383,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "n_fluid_cells": n_fluid,
-        "nonfinite_cells": red[4],
+        "nonfinite_cells": bad,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -138,6 +138,10 @@ typedef struct {
     int32_t n_members;
     int32_t precision;
     int64_t launches;       /* kernels this context has launched so far              */
+    int32_t variant;        /* launch shape of the step kernel (lbm_set_variant)     */
+    int32_t step_threads;   /* threads per block of that shape                       */
+    int32_t n_variants;     /* launch shapes available for this precision            */
+    int32_t graph_chunk;    /* steps per captured graph, 0 = direct launches         */
 } lbm_info;
 
 /* ==== life cycle ====================================================================== */
@@ -196,6 +200,27 @@ int lbm_init_fields(lbm_ctx *ctx, const double *rho, const double *u);
  * accumulate the statistics (lbm_stats_enable).  Asynchronous unless a stability
  * check is due (lbm_set_check), which synchronises and may return LBM_EUNSTABLE. */
 int lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Steps in CUDA graphs: from now on lbm_step replays a captured graph of `chunk`
+ * steps (even, 2..4096; 0 = direct launches) whenever at least `chunk` steps remain
+ * and t is even (and a multiple of the statistics interval when statistics are on);
+ * the rest run as direct launches.  The graph is captured once per launch shape and
+ * statistics setting; every node reads its step index and trigger phase from a
+ * device table that the host refreshes before each replay, so results are
+ * bit-identical to direct launches.  Allocates the tables (device + pinned host). */
+int lbm_set_graph(lbm_ctx *ctx, int32_t chunk);
+
+/* Launch shape ("variant") of the step kernel: 0 = 256 threads, registers for 4
+ * blocks per SM; 1 = 256 x 3; 2 = 128 x 8; 3 = 512 x 2.  LBM_F64 has one shape (256 x
+ * 2).  The arithmetic per cell is the same for every shape: results are
+ * bit-identical. */
+int lbm_set_variant(lbm_ctx *ctx, int32_t variant);
+
+/* Project autotuner for the launch shape: times `steps` steps (2..10000) of every
+ * shape on the context's own problem, restores the populations, t and statistics
+ * afterwards, selects the fastest shape and returns it with its time per step
+ * (microseconds).  Synchronises; allocates one temporary copy of the populations. */
+int lbm_autotune(lbm_ctx *ctx, int32_t steps, int32_t *variant, double *best_us);
 
 /* Every `every` steps (0 = never), lbm_step reduces mass and checks for
  * non-finite populations; a relative mass drift above max_mass_drift or any

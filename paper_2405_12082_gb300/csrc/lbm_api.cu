@@ -24,7 +24,6 @@ struct lbm_ctx {
     void *pops = nullptr;
     int64_t stride = 0;              // cells per population plane
     size_t esize = 0;                // bytes per stored population
-    int32_t nblocks = 0;
     int64_t t = 0;
     float f16_scale = 1.f, f16_inv = 1.f;
     double *stats = nullptr;
@@ -41,7 +40,18 @@ struct lbm_ctx {
     bool prof = false;
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
+    std::vector<int64_t> ev_launches;   // step kernels covered by each timed event pair
+    int64_t prof_launches_pending = 0;
     int64_t launches = 0;
+    int variant = 0;                 // launch shape of the step kernel
+    // graph-captured chunks of steps
+    int32_t graph_chunk = 0;
+    cudaGraphExec_t gexec = nullptr;
+    int gexec_variant = -1, gexec_stats_every = -1;
+    lbm::StepTime *d_times = nullptr;        // [graph_chunk] device table read by the graph
+    lbm::StepTime *h_times[2] = {nullptr, nullptr};   // pinned staging, double-buffered
+    cudaEvent_t h_done[2] = {nullptr, nullptr};
+    int h_next = 0;
     std::string err;
 };
 
@@ -218,18 +228,31 @@ StepArgs make_args(const lbm_ctx *c, int64_t t) {
     a.stride = c->stride;
     a.members = c->dm;
     a.n_members = (int32_t)c->hm.size();
-    a.nblocks_total = c->nblocks;
     a.t = t;
     a.f16_scale = c->f16_scale;
     a.f16_inv = c->f16_inv;
     a.stats = c->stats;
+    const int bs = lbm::step_threads(c->precision, c->variant);
+    int64_t blk = 0;
     for (size_t m = 0; m < c->hm.size(); ++m) {
         const Member &d = c->hm[m];
         a.st[m] = (d.trig && t < d.t_end) ? std::sin(2.0 * M_PI * (double)t / d.period) : 0.0;
-        a.block0[m] = (int32_t)d.block0;
+        a.block0[m] = (int32_t)blk;
+        blk += (d.cells + bs - 1) / bs;
     }
-    a.block0[c->hm.size()] = c->nblocks;
+    a.block0[c->hm.size()] = (int32_t)blk;
+    a.nblocks_total = (int32_t)blk;
+    a.times = nullptr;
+    a.tidx = 0;
     return a;
+}
+
+void fill_times(const lbm_ctx *c, lbm::StepTime &st, int64_t t) {
+    st.t = t;
+    for (size_t m = 0; m < c->hm.size(); ++m) {
+        const Member &d = c->hm[m];
+        st.st[m] = (d.trig && t < d.t_end) ? std::sin(2.0 * M_PI * (double)t / d.period) : 0.0;
+    }
 }
 
 int upload_members(lbm_ctx *c) {
@@ -287,9 +310,8 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
         int rc = build_member(nullptr, &grids[k], &relax[k], force ? &force[k] : nullptr, c->hm[k]);
         if (rc) { delete c; return rc; }
         c->hm[k].off = off;
-        c->hm[k].block0 = blk;
         off += ceil_div(c->hm[k].cells, 64) * 64;   // keep every member 64-cell aligned
-        blk += ceil_div(c->hm[k].cells, lbm::STEP_BLOCK_HOST);
+        blk += ceil_div(c->hm[k].cells, 128);        // the smallest launch shape
         c->grids.push_back(grids[k]);
         lbm_force fz;
         std::memset(&fz, 0, sizeof fz);
@@ -302,7 +324,6 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
                        "27 x %lld cells exceed the 32-bit population index of the step kernels", (long long)off);
     }
     c->stride = off;
-    c->nblocks = (int32_t)blk;
     c->esize = esize_of(prec);
     c->mass0.assign(n, 0.0);
     c->mass0_valid.assign(n, false);
@@ -403,6 +424,7 @@ int event_pair(lbm_ctx *c, cudaEvent_t &a, cudaEvent_t &b) {
     a = c->ev[c->ev_used];
     b = c->ev[c->ev_used + 1];
     c->ev_used += 2;
+    c->ev_launches.push_back(0);
     return LBM_OK;
 }
 
@@ -429,6 +451,12 @@ void lbm_free(lbm_ctx *c) {
     cudaFree(c->scratch);
     cudaFree(c->partials);
     cudaFree(c->geo);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    cudaFree(c->d_times);
+    for (int b = 0; b < 2; ++b) {
+        if (c->h_times[b]) cudaFreeHost(c->h_times[b]);
+        if (c->h_done[b]) cudaEventDestroy(c->h_done[b]);
+    }
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     cudaGetLastError();
     delete c;
@@ -461,6 +489,10 @@ int lbm_get_info(lbm_ctx *c, lbm_info *info) {
     info->n_members = (int32_t)c->hm.size();
     info->precision = c->precision;
     info->launches = c->launches;
+    info->variant = c->variant;
+    info->step_threads = lbm::step_threads(c->precision, c->variant);
+    info->n_variants = lbm::step_variants(c->precision);
+    info->graph_chunk = c->graph_chunk;
     return LBM_OK;
 }
 
@@ -547,31 +579,239 @@ int lbm_set_check(lbm_ctx *c, int64_t every, double max_mass_drift) {
     return LBM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// One step by a direct launch.
+int step_direct(lbm_ctx *c) {
+    const bool stats = c->stats && c->stats_every > 0 && (c->t % c->stats_every == 0);
+    const StepArgs a = make_args(c, c->t);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->prof) {
+        int rc = event_pair(c, e0, e1);
+        if (rc) return rc;
+        LBM_CUDA(c, cudaEventRecord(e0, c->stream));
+    }
+    int rc = dispatch(c, [&](auto P) {
+        return lbm::launch_step<decltype(P)::value>(c->wall, (int)(c->t & 1), stats, a, c->variant, c->stream);
+    });
+    if (rc) return rc;
+    if (c->prof) {
+        LBM_CUDA(c, cudaEventRecord(e1, c->stream));
+        c->ev_launches.back() += 1;
+    }
+    c->t++;
+    if (stats) c->stats_count++;
+    return LBM_OK;
+}
+
+void drop_graph(lbm_ctx *c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gexec_variant = -1;
+    c->gexec_stats_every = -1;
+}
+
+// Captures graph_chunk steps that start at an even t (and, with statistics on, at a
+// multiple of the statistics interval); every node reads its step index and trigger
+// phase from d_times[k], so one instantiated graph serves every replay.
+int build_graph(lbm_ctx *c) {
+    drop_graph(c);
+    const int every = (c->stats && c->stats_every > 0) ? c->stats_every : 0;
+    cudaStream_t cs;
+    LBM_CUDA(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return cuda_err(c, e, "cudaStreamBeginCapture");
+    }
+    StepArgs a = make_args(c, 0);
+    a.times = c->d_times;
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < c->graph_chunk && le == cudaSuccess; ++k) {
+        a.tidx = k;
+        const bool stats = every > 0 && (k % every == 0);
+        switch (c->precision) {
+            case LBM_F64: le = lbm::launch_step<LBM_F64>(c->wall, k & 1, stats, a, c->variant, cs); break;
+            case LBM_F32: le = lbm::launch_step<LBM_F32>(c->wall, k & 1, stats, a, c->variant, cs); break;
+            case LBM_F16S: le = lbm::launch_step<LBM_F16S>(c->wall, k & 1, stats, a, c->variant, cs); break;
+            default: le = lbm::launch_step<LBM_BF16>(c->wall, k & 1, stats, a, c->variant, cs); break;
+        }
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_err(c, le, "capture of the step chunk");
+    }
+    if (e != cudaSuccess) return cuda_err(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_err(c, e, "cudaGraphInstantiate");
+    }
+    c->gexec_variant = c->variant;
+    c->gexec_stats_every = every;
+    return LBM_OK;
+}
+
+// One replay of the captured chunk starting at the current (aligned) t.
+int step_graph_chunk(lbm_ctx *c) {
+    const int every = (c->stats && c->stats_every > 0) ? c->stats_every : 0;
+    if (!c->gexec || c->gexec_variant != c->variant || c->gexec_stats_every != every) {
+        int rc = build_graph(c);
+        if (rc) return rc;
+    }
+    const int b = c->h_next;
+    c->h_next ^= 1;
+    LBM_CUDA(c, cudaEventSynchronize(c->h_done[b]));   // staging buffer b is free again
+    for (int k = 0; k < c->graph_chunk; ++k) fill_times(c, c->h_times[b][k], c->t + k);
+    LBM_CUDA(c, cudaMemcpyAsync(c->d_times, c->h_times[b], sizeof(lbm::StepTime) * c->graph_chunk,
+                                cudaMemcpyHostToDevice, c->stream));
+    LBM_CUDA(c, cudaEventRecord(c->h_done[b], c->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->prof) {
+        int rc = event_pair(c, e0, e1);
+        if (rc) return rc;
+        LBM_CUDA(c, cudaEventRecord(e0, c->stream));
+    }
+    LBM_CUDA(c, cudaGraphLaunch(c->gexec, c->stream));
+    if (c->prof) {
+        LBM_CUDA(c, cudaEventRecord(e1, c->stream));
+        c->ev_launches.back() += c->graph_chunk;
+    }
+    c->launches += c->graph_chunk;
+    if (every > 0) c->stats_count += (c->graph_chunk + every - 1) / every;
+    c->t += c->graph_chunk;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int lbm_step(lbm_ctx *c, int64_t n) {
     if (!c) return LBM_EINVAL;
     if (n < 0) return set_err(c, LBM_EINVAL, "n must be >= 0");
-    for (int64_t k = 0; k < n; ++k) {
-        const bool stats = c->stats && c->stats_every > 0 && (c->t % c->stats_every == 0);
-        const StepArgs a = make_args(c, c->t);
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (c->prof) {
-            int rc = event_pair(c, e0, e1);
-            if (rc) return rc;
-            LBM_CUDA(c, cudaEventRecord(e0, c->stream));
+    while (n > 0) {
+        const int every = (c->stats && c->stats_every > 0) ? c->stats_every : 0;
+        const int64_t t0 = c->t;
+        const bool aligned = (c->t % 2 == 0) && (every == 0 || c->t % every == 0);
+        int rc;
+        int64_t done;
+        if (c->graph_chunk > 0 && n >= c->graph_chunk && aligned) {
+            rc = step_graph_chunk(c);
+            done = c->graph_chunk;
+        } else {
+            rc = step_direct(c);
+            done = 1;
         }
-        int rc = dispatch(c, [&](auto P) {
-            return lbm::launch_step<decltype(P)::value>(c->wall, (int)(c->t & 1), stats, a, lbm::STEP_BLOCK_HOST,
-                                                        c->stream);
-        });
         if (rc) return rc;
-        if (c->prof) LBM_CUDA(c, cudaEventRecord(e1, c->stream));
-        c->t++;
-        if (stats) c->stats_count++;
-        if (c->check_every > 0 && c->t % c->check_every == 0) {
+        n -= done;
+        if (c->check_every > 0 && (c->t / c->check_every) != (t0 / c->check_every)) {
             rc = stability_check(c);
             if (rc) return rc;
         }
     }
+    return LBM_OK;
+}
+
+int lbm_set_graph(lbm_ctx *c, int32_t chunk) {
+    if (!c) return LBM_EINVAL;
+    if (chunk != 0 && (chunk < 2 || chunk > 4096 || (chunk & 1)))
+        return set_err(c, LBM_EINVAL, "graph chunk must be 0 or an even number in 2..4096");
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    drop_graph(c);
+    cudaFree(c->d_times);
+    c->d_times = nullptr;
+    for (int b = 0; b < 2; ++b) {
+        if (c->h_times[b]) cudaFreeHost(c->h_times[b]);
+        c->h_times[b] = nullptr;
+        if (c->h_done[b]) cudaEventDestroy(c->h_done[b]);
+        c->h_done[b] = nullptr;
+    }
+    c->graph_chunk = 0;
+    if (chunk == 0) return LBM_OK;
+    const size_t bytes = sizeof(lbm::StepTime) * chunk;
+    cudaError_t e = cudaMalloc((void **)&c->d_times, bytes);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaMallocHost((void **)&c->h_times[b], bytes);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->h_done[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(c->h_done[b], c->stream);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        lbm_set_graph(c, 0);
+        return set_err(c, LBM_ENOMEM, "cannot allocate the step tables of the graph");
+    }
+    c->graph_chunk = chunk;
+    return LBM_OK;
+}
+
+int lbm_set_variant(lbm_ctx *c, int32_t variant) {
+    if (!c) return LBM_EINVAL;
+    if (variant < 0 || variant >= lbm::step_variants(c->precision))
+        return set_err(c, LBM_EINVAL, "launch-shape variant %d out of range (0..%d)", variant,
+                       lbm::step_variants(c->precision) - 1);
+    c->variant = variant;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *variant, double *best_us) {
+    if (!c) return LBM_EINVAL;
+    if (steps < 2 || steps > 10000) return set_err(c, LBM_EINVAL, "steps must be in 2..10000");
+    const int nv = lbm::step_variants(c->precision);
+    const size_t bytes = (size_t)27 * c->stride * c->esize;
+    void *save = nullptr;
+    if (cudaMalloc(&save, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, LBM_ENOMEM, "cannot allocate the state copy for autotuning");
+    }
+    LBM_CUDA(c, cudaMemcpyAsync(save, c->pops, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    const int64_t t_save = c->t, count_save = c->stats_count, launches_save = c->launches;
+    double *stats_save = c->stats;
+    const int64_t check_save = c->check_every;
+    const bool prof_save = c->prof;
+    c->stats = nullptr;          // no statistics, checks or profiling while tuning
+    c->check_every = 0;
+    c->prof = false;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0, rc = LBM_OK;
+    double best_t = 1e300;
+    for (int v = 0; v < nv && rc == LBM_OK; ++v) {
+        c->variant = v;
+        c->t = t_save;
+        for (int k = 0; k < 2 && rc == LBM_OK; ++k) rc = step_direct(c);
+        if (rc) break;
+        cudaEventRecord(e0, c->stream);
+        for (int k = 0; k < steps && rc == LBM_OK; ++k) rc = step_direct(c);
+        cudaEventRecord(e1, c->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = cuda_err(c, cudaGetLastError(), "autotune"); break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double us = 1e3 * ms / steps;
+        if (us < best_t) { best_t = us; best = v; }
+        cudaMemcpyAsync(c->pops, save, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(save);
+    c->t = t_save;
+    c->stats = stats_save;
+    c->stats_count = count_save;
+    c->check_every = check_save;
+    c->prof = prof_save;
+    c->launches = launches_save;
+    c->variant = best;
+    if (rc) return rc;
+    if (variant) *variant = best;
+    if (best_us) *best_us = best_t;
     return LBM_OK;
 }
 
@@ -759,14 +999,17 @@ int lbm_profile_read(lbm_ctx *c, double *ms, int64_t *launches) {
     if (!c) return LBM_EINVAL;
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     double total = 0;
+    int64_t n = 0;
     for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
         float x = 0;
         LBM_CUDA(c, cudaEventElapsedTime(&x, c->ev[k], c->ev[k + 1]));
         total += x;
+        n += c->ev_launches[k / 2];
     }
     if (ms) *ms = total;
-    if (launches) *launches = (int64_t)(c->ev_used / 2);
+    if (launches) *launches = n;
     c->ev_used = 0;
+    c->ev_launches.clear();
     return LBM_OK;
 }
 

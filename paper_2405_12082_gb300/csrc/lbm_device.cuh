@@ -126,6 +126,13 @@ __device__ __forceinline__ uint32_t fastdiv(uint32_t n, uint32_t mul, uint32_t s
     return shr == 0xFFFFFFFFu ? n : (__umulhi(n, mul) >> shr);
 }
 
+// Per-step values for graph-captured chunks of steps: step index and sin(2 pi t / T) of
+// every member's trigger (0 when off), filled by the host before each replay.
+struct StepTime {
+    int64_t t;
+    double st[LBM_MAX_MEMBERS];
+};
+
 struct StepArgs {
     void *pops;               // [27][stride] storage elements
     int64_t stride;           // cells per population plane (all members)
@@ -137,6 +144,8 @@ struct StepArgs {
     double *stats;            // [4][stride] FP64 accumulators (sample steps)
     double st[LBM_MAX_MEMBERS];      // sin(2 pi t / T) per member (0 when off)
     int32_t block0[LBM_MAX_MEMBERS + 1];
+    const StepTime *times;    // when set, t and st come from times[tidx] (graph replays)
+    int32_t tidx;
 };
 
 __device__ __forceinline__ int find_member(const StepArgs &a, int blk) {

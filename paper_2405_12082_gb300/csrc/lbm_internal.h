@@ -14,10 +14,21 @@ struct ModesArgs {
     double r_over_R[16];
 };
 
+// Launch shapes of the step kernel ("variants"): threads per block and the number of
+// resident blocks per SM the register budget is cut for.  FP64 storage has one shape.
+struct StepShape { int threads, min_blocks; };
+constexpr StepShape STEP_SHAPES[4] = {{256, 4}, {256, 3}, {128, 8}, {512, 2}};
+constexpr StepShape STEP_SHAPE_F64 = {256, 2};
+inline int step_variants(int precision) { return precision == LBM_F64 ? 1 : 4; }
+inline int step_threads(int precision, int variant) {
+    return precision == LBM_F64 ? STEP_SHAPE_F64.threads : STEP_SHAPES[variant].threads;
+}
+
 // Every launcher enqueues on `s` and returns the launch status.
-// Step kernel over all members (flat grid of a.nblocks_total blocks of `block` threads).
+// Step kernel over all members: a flat grid of a.nblocks_total blocks of
+// step_threads(P, variant) threads.
 template <int P>
-cudaError_t launch_step(int wall, int parity, bool stats, const StepArgs &a, int block, cudaStream_t s);
+cudaError_t launch_step(int wall, int parity, bool stats, const StepArgs &a, int variant, cudaStream_t s);
 
 // Per-member kernels: member m of a.members (host copy hm for sizes).
 template <int P>
@@ -45,10 +56,6 @@ template <int P>
 cudaError_t launch_force_tables(const Member *dmembers, const Member &hm, int m, void *ftab, void *ztab,
                                 cudaStream_t s);
 
-#ifndef LBM_STEP_BLOCK
-#define LBM_STEP_BLOCK 256
-#endif
-constexpr int STEP_BLOCK_HOST = LBM_STEP_BLOCK;   // threads per block of the step kernel
 constexpr int REDUCE_BLOCK = 256;
 constexpr int REDUCE_MAX_BLOCKS = 1216;   // 8 resident blocks x 152 SMs
 

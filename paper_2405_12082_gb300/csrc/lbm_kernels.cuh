@@ -9,29 +9,26 @@
 
 namespace lbm {
 
-constexpr int STEP_BLOCK = STEP_BLOCK_HOST;
-#ifndef LBM_STEP_MIN_BLOCKS
-#define LBM_STEP_MIN_BLOCKS 4
-#endif
-constexpr int STEP_MIN_BLOCKS = LBM_STEP_MIN_BLOCKS;   // resident blocks per SM the registers must allow
-
 // ---- the fused step: load (stream) + wall + force + MRT collision + store ----------------
 // One thread per cell of every member; solid cells return at once.  On sample
 // steps (STATS) u_z^k, k = 1..4, of the pre-collision state is added in FP64.
-template <int P, int PAR, int WALL, bool STATS>
-__global__ void __launch_bounds__(STEP_BLOCK, STEP_MIN_BLOCKS) k_step(const __grid_constant__ StepArgs a) {
+// BS threads per block, register budget for MINB resident blocks per SM.
+template <int P, int PAR, int WALL, bool STATS, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_step(const __grid_constant__ StepArgs a) {
     using R = typename Storage<P>::R;
     const int m = find_member(a, blockIdx.x);
     const Member &d = a.members[m];
-    const uint32_t local = (uint32_t)(blockIdx.x - a.block0[m]) * STEP_BLOCK + threadIdx.x;
+    const uint32_t local = (uint32_t)(blockIdx.x - a.block0[m]) * BS + threadIdx.x;
     if (local >= (uint32_t)d.cells) return;
     CellPos p;
     cell_setup(d, local, p);
     if (!((p.nb >> 4) & 1u)) return;
+    const int64_t t = a.times ? a.times[a.tidx].t : a.t;
+    const double stv = a.times ? a.times[a.tidx].st[m] : a.st[m];
     R v[Q];
     load_pops<P, PAR, WALL>(a, d, p, v);
     R gx, gy, gz;
-    acceleration<R>(d, p, a.t, a.st[m], gx, gy, gz);
+    acceleration<R>(d, p, t, stv, gx, gy, gz);
     const Macro<R> mm = collide<R>(v, gx, gy, gz, (R)d.omega);
     if constexpr (STATS) {
         const double uz = (double)mm.uz;
@@ -397,15 +394,28 @@ __global__ void k_force_tables(const Member *members, int m, R *ftab, R *ztab) {
 
 static inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-template <int P>
-cudaError_t launch_step(int wall, int parity, bool stats, const StepArgs &a, int block, cudaStream_t s) {
-    (void)block;
-    if (a.nblocks_total <= 0) return cudaSuccess;
+template <int P, int BS, int MINB>
+cudaError_t launch_step_shape(int wall, int parity, bool stats, const StepArgs &a, cudaStream_t s) {
     LBM_DISPATCH_WP(wall, parity, {
-        if (stats) k_step<P, PA, W, true><<<a.nblocks_total, STEP_BLOCK, 0, s>>>(a);
-        else k_step<P, PA, W, false><<<a.nblocks_total, STEP_BLOCK, 0, s>>>(a);
+        if (stats) k_step<P, PA, W, true, BS, MINB><<<a.nblocks_total, BS, 0, s>>>(a);
+        else k_step<P, PA, W, false, BS, MINB><<<a.nblocks_total, BS, 0, s>>>(a);
     });
     return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_step(int wall, int parity, bool stats, const StepArgs &a, int variant, cudaStream_t s) {
+    if (a.nblocks_total <= 0) return cudaSuccess;
+    if constexpr (P == LBM_F64) {
+        return launch_step_shape<P, 256, 2>(wall, parity, stats, a, s);
+    } else {
+        switch (variant) {
+            case 1: return launch_step_shape<P, 256, 3>(wall, parity, stats, a, s);
+            case 2: return launch_step_shape<P, 128, 8>(wall, parity, stats, a, s);
+            case 3: return launch_step_shape<P, 512, 2>(wall, parity, stats, a, s);
+            default: return launch_step_shape<P, 256, 4>(wall, parity, stats, a, s);
+        }
+    }
 }
 
 template <int P>

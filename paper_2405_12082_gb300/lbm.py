@@ -65,7 +65,8 @@ class lbm_modes_cfg(ctypes.Structure):
 class lbm_info(ctypes.Structure):
     _fields_ = [("n_cells", ctypes.c_int64), ("n_fluid", ctypes.c_int64), ("t", ctypes.c_int64),
                 ("population_bytes", ctypes.c_int64), ("n_members", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("launches", ctypes.c_int64)]
+                ("precision", ctypes.c_int32), ("launches", ctypes.c_int64), ("variant", ctypes.c_int32),
+                ("step_threads", ctypes.c_int32), ("n_variants", ctypes.c_int32), ("graph_chunk", ctypes.c_int32)]
 
 
 def _load():
@@ -102,6 +103,9 @@ def _load():
         "lbm_profile_read": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
         "lbm_fluid_mask": [P, P],
         "lbm_reduce_static": [P, I32, I32, I64, P, P],
+        "lbm_set_graph": [P, I32],
+        "lbm_set_variant": [P, I32],
+        "lbm_autotune": [P, I32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -120,7 +124,7 @@ EXPORTED = ("lbm_create", "lbm_ensemble_create", "lbm_free", "lbm_last_error", "
             "lbm_init_fields", "lbm_step", "lbm_set_check", "lbm_moments", "lbm_get_populations",
             "lbm_set_populations", "lbm_get_raw", "lbm_set_raw", "lbm_reduce", "lbm_stats_enable",
             "lbm_stats_get", "lbm_modes", "lbm_adjoint", "lbm_profile_enable", "lbm_profile_read",
-            "lbm_fluid_mask", "lbm_reduce_static")
+            "lbm_fluid_mask", "lbm_reduce_static", "lbm_set_graph", "lbm_set_variant", "lbm_autotune")
 
 
 # ---- marshalling helpers -----------------------------------------------------------------
@@ -314,6 +318,21 @@ def lbm_profile_read(ctx):
     n = ctypes.c_int64()
     _check(ctx, LIB.lbm_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def lbm_set_graph(ctx, chunk):
+    return _check(ctx, LIB.lbm_set_graph(ctx, int(chunk)))
+
+
+def lbm_set_variant(ctx, variant):
+    return _check(ctx, LIB.lbm_set_variant(ctx, int(variant)))
+
+
+def lbm_autotune(ctx, steps):
+    v = ctypes.c_int32()
+    us = ctypes.c_double()
+    _check(ctx, LIB.lbm_autotune(ctx, int(steps), ctypes.byref(v), ctypes.byref(us)))
+    return v.value, us.value
 
 
 def lbm_fluid_mask(ctx, mask):

@@ -42,7 +42,8 @@ C3 = dict(C2, name="turbulent pipe 196x196x1152 R=96", nx=196, ny=196, nz=1152, 
 
 # Batched ensemble: 16 pipes, R drawn from {16, 20, 24, 32}, length 256, tau = 0.5096.
 C4 = dict(name="ensemble 16 pipes R in {16,20,24,32} L=256", n=16, radii=(16, 20, 24, 32), nz=256,
-          nu=0.0032, omega=1.9623233908948192, u_star=0.00388, steps=5000, precision="f32", wall="halfway")
+          nu=0.0032, omega=1.9623233908948192, u_star=0.00388, noise=0.0028518, steps=5000, precision="f32",
+          wall="halfway")
 
 # Adjoint: 52 x 52 x 256, R = 24, tau = 0.8, per-cell g_z = 1e-6, T = 2000.
 C5 = dict(name="adjoint pipe 52x52x256 R=24", nx=52, ny=52, nz=256, R=24.0, nu=0.1, omega=1.25, gz=1e-6,
@@ -59,13 +60,18 @@ def trigger_dict(h, R, nz, period, modes, t_end, A0=50.0, kappa=0.5, kz=3):
                 modes=list(modes))
 
 
-def ensemble_members(seed=SEED, n=16, radii=(16, 20, 24, 32)):
+def ensemble_members(seed=SEED, n=16, radii=(16, 20, 24, 32), u_star=0.00388):
     """Seeded member list: radius drawn uniformly from `radii`, noise seed base + k and
-    trigger phase 2 pi k / n for member k."""
+    trigger phase 2 pi k / n for member k; per radius the body force h = 2 u*^2 / R, the
+    trigger period 0.052 R / u* and a trigger lasting 3 R / u* steps (configuration)."""
     rng = np.random.default_rng(seed)
     Rs = rng.choice(np.array(radii), size=n)
-    return [dict(R=float(Rs[k]), seed=seed + k, phase=2.0 * math.pi * k / n,
-                 h=2.0 * 0.00388 ** 2 / float(Rs[k])) for k in range(n)]
+    out = []
+    for k in range(n):
+        R = float(Rs[k])
+        out.append(dict(R=R, seed=seed + k, phase=2.0 * math.pi * k / n, h=2.0 * u_star ** 2 / R,
+                        period=0.052 * R / u_star, t_end=int(3 * R / u_star)))
+    return out
 
 
 def gz_field(nz, ny, nx, base, seed=SEED, rel_amp=0.0, dtype=np.float64):

@@ -63,7 +63,7 @@ def test_struct_layouts_match_the_header(lbm_lib):
     assert ctypes.sizeof(lbm.lbm_relax) == 8
     assert ctypes.sizeof(lbm.lbm_force) == 264
     assert ctypes.sizeof(lbm.lbm_modes_cfg) == 144
-    assert ctypes.sizeof(lbm.lbm_info) == 48
+    assert ctypes.sizeof(lbm.lbm_info) == 64
 
 
 def test_struct_layouts_match_a_c_compiler(lbm_lib, tmp_path):
@@ -78,7 +78,7 @@ def test_struct_layouts_match_a_c_compiler(lbm_lib, tmp_path):
         "lbm_grid": ["nx", "R", "precision", "wall", "f16_log2_scale"],
         "lbm_force": ["g", "trigger", "n_modes", "k_theta", "weight", "phase", "A0", "h", "kz", "t_end", "gz_field"],
         "lbm_modes_cfg": ["n_sections", "r_over_R", "n_theta", "n_modes"],
-        "lbm_info": ["n_cells", "population_bytes", "n_members", "precision", "launches"],
+        "lbm_info": ["n_cells", "population_bytes", "n_members", "precision", "launches", "variant", "graph_chunk"],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm.h"', "int main(void){"]
     for st, fields in checks.items():
