@@ -153,7 +153,7 @@ def forcing_printed(rho, u, F):
 
 def relaxation_diag(omega):
     """Eq. (lambda): Lambda = diag[1,1,1,1, omega x5, 1 x18]."""
-    lam = np.ones(27)
+    lam = np.ones(27, dtype=np.result_type(omega, np.float64))   # complex omega: complex-step derivatives
     lam[4:9] = omega
     return lam
 
