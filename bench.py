@@ -40,9 +40,10 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"])
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"])
     p.add_argument("--graph", type=int, default=None, help="steps per captured graph (0 = direct launches)")
     p.add_argument("--autotune", action="store_true", help="pick the step-kernel launch shape by timing")
+    p.add_argument("--variant", type=int, default=None, help="force a step-kernel launch shape")
     p.add_argument("--precision", default="f32", choices=["f32", "f16s", "bf16", "f64"])
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -50,7 +51,7 @@ def parse():
 
 
 def workload(name):
-    return dict({"c2": Wk.C2, "c3": Wk.C3, "c4": Wk.C4}[name])
+    return dict({"c2": Wk.C2, "c3": Wk.C3, "c4": Wk.C4, "c5": Wk.C5}[name])
 
 
 def config_json(cfg, args, n_gpus, graph=0, tuned=None):
@@ -278,7 +279,10 @@ def run_ours(args):
         cells.append(mi["n_cells"])
     L.select(0)
     tuned = None
-    if args.autotune or ensemble:
+    if args.variant is not None:
+        lbm.lbm_set_variant(L.ctx, args.variant)
+        tuned = (args.variant, None)
+    elif args.autotune or ensemble:
         tuned = lbm.lbm_autotune(L.ctx, 20)
     graph = args.graph if args.graph is not None else (LBM_STEPS_PER_STEP if ensemble else 0)
     if graph:
@@ -391,10 +395,63 @@ def run_ours(args):
     return 0
 
 
+def run_adjoint_bench(args):
+    """Forward MLUPS and the adjoint/forward time ratio on the 52 x 52 x 256, R = 24 pipe
+    (T = 2000 steps, FP32, per-cell axial acceleration): the adjoint call runs its own
+    forward pass with checkpoints, recomputes every segment and sweeps backwards."""
+    import numpy as np
+    import torch
+    from paper_2405_12082_gb300 import lbm
+    cfg = workload("c5")
+    prec = args.precision
+    dt = torch.float64 if prec == "f64" else torch.float32
+    gz = torch.full((cfg["nz"], cfg["ny"], cfg["nx"]), cfg["gz"], dtype=dt, device="cuda")
+    grid = lbm.make_grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["R"], precision=prec, wall="halfway")
+    stream = torch.cuda.current_stream()
+    L = lbm.Lattice(grid, lbm.lbm_relax(cfg["omega"]), lbm.make_force(gz_field=gz), stream=stream.cuda_stream)
+    L.init("rest")
+    n_fluid = L.info()["n_fluid"]
+    T = cfg["T"]
+    L.step(200)
+    dgz = torch.zeros_like(gz, dtype=torch.float64)
+    lbm.lbm_adjoint(L.ctx, 50, lbm.LBM_J_UBULK, 0, dgz)      # warm-up of the adjoint path
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fwd = []
+    for _ in range(max(args.steps, 1)):
+        e0.record(stream)
+        L.step(T)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fwd.append(e0.elapsed_time(e1))
+    adj = []
+    for _ in range(max(args.steps, 1)):
+        e0.record(stream)
+        J, dw = lbm.lbm_adjoint(L.ctx, T, lbm.LBM_J_UBULK, 0, dgz)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        adj.append(e0.elapsed_time(e1))
+    L.close()
+    f_ms, a_ms = min(fwd), min(adj)
+    line = {"metric": METRIC + "; adjoint/forward time ratio", "value": n_fluid * T / (f_ms * 1e-3) / 1e6,
+            "unit": "MLUPS", "n_gpus": 1, "steps": len(fwd), "warmup": 1, "ms_per_step": f_ms / T,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "f64" else "f32", "storage": prec, "data": "synthetic (rest start)",
+            "config": {"workload": cfg["name"], "grid": [cfg["nx"], cfg["ny"], cfg["nz"]], "R": cfg["R"],
+                       "T": T, "checkpoints": "every ceil(sqrt(T)) steps", "objective": "bulk velocity"},
+            "adjoint": {"forward_ms": f_ms, "adjoint_call_ms": a_ms,
+                        "reverse_over_forward": (a_ms - f_ms) / f_ms, "total_over_forward": a_ms / f_ms,
+                        "J": J, "dJ_domega": dw}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c5":
+        return run_adjoint_bench(args)
     return run_ours(args)
 
 

@@ -211,9 +211,11 @@ int lbm_step(lbm_ctx *ctx, int64_t n);
 int lbm_set_graph(lbm_ctx *ctx, int32_t chunk);
 
 /* Launch shape ("variant") of the step kernel: 0 = 256 threads, registers for 4
- * blocks per SM; 1 = 256 x 3; 2 = 128 x 8; 3 = 512 x 2.  LBM_F64 has one shape (256 x
- * 2).  The arithmetic per cell is the same for every shape: results are
- * bit-identical. */
+ * blocks per SM; 1 = 256 x 3; 2 = 128 x 8; 3 = 512 x 2; for LBM_F32 also the
+ * software-pipelined persistent kernel, 4 = 256 x 3 and 5 = 128 x 6 (each thread
+ * copies its next cell's 27 populations into shared memory with cp.async while it
+ * computes the current one).  LBM_F64 has one shape (256 x 2).  The arithmetic per
+ * cell is the same for every shape. */
 int lbm_set_variant(lbm_ctx *ctx, int32_t variant);
 
 /* Project autotuner for the launch shape: times `steps` steps (2..10000) of every

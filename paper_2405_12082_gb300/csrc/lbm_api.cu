@@ -1,4 +1,5 @@
 // lbm_api.cu -- the C ABI of include/lbm.h: contexts, validation, memory, launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -157,7 +158,10 @@ int check_force(lbm_ctx *c, const lbm_force *f) {
 }
 
 void fill_force(Member &d, const lbm_force *f) {
-    for (int k = 0; k < 3; ++k) d.g[k] = f ? f->g[k] : 0.0;
+    for (int k = 0; k < 3; ++k) {
+        d.g[k] = f ? f->g[k] : 0.0;
+        d.gf[k] = (float)d.g[k];
+    }
     d.trig = (f && f->trigger) ? 1 : 0;
     d.n_modes = d.trig ? f->n_modes : 0;
     d.kz = f ? f->kz : 0;
@@ -190,6 +194,7 @@ int build_member(lbm_ctx *c, const lbm_grid *g, const lbm_relax *r, const lbm_fo
     d.cells = cells;
     d.R = g->R;
     d.omega = r->omega;
+    d.omegaf = (float)r->omega;
     if (g->geometry == LBM_PIPE) {
         if (g->nx < 3 || g->ny < 3) return set_err(c, LBM_EINVAL, "a pipe needs nx, ny >= 3");
         if (!(g->R > 0.0) || !std::isfinite(g->R)) return set_err(c, LBM_EINVAL, "pipe radius must be > 0");
@@ -237,6 +242,7 @@ StepArgs make_args(const lbm_ctx *c, int64_t t) {
     for (size_t m = 0; m < c->hm.size(); ++m) {
         const Member &d = c->hm[m];
         a.st[m] = (d.trig && t < d.t_end) ? std::sin(2.0 * M_PI * (double)t / d.period) : 0.0;
+        a.stf[m] = (float)a.st[m];
         a.block0[m] = (int32_t)blk;
         blk += (d.cells + bs - 1) / bs;
     }
@@ -252,6 +258,7 @@ void fill_times(const lbm_ctx *c, lbm::StepTime &st, int64_t t) {
     for (size_t m = 0; m < c->hm.size(); ++m) {
         const Member &d = c->hm[m];
         st.st[m] = (d.trig && t < d.t_end) ? std::sin(2.0 * M_PI * (double)t / d.period) : 0.0;
+        st.stf[m] = (float)st.st[m];
     }
 }
 
@@ -500,6 +507,7 @@ int lbm_set_relax(lbm_ctx *c, const lbm_relax *r) {
     if (!c || !r) return LBM_EINVAL;
     if (!(r->omega > 0.0 && r->omega < 2.0)) return set_err(c, LBM_EINVAL, "omega must be in (0, 2)");
     c->hm[c->sel].omega = r->omega;
+    c->hm[c->sel].omegaf = (float)r->omega;
     return upload_members(c);
 }
 
@@ -984,9 +992,123 @@ int lbm_modes(lbm_ctx *c, const lbm_modes_cfg *cfg, double *E) {
 
 int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_every, double *J, double *dJ_dgz,
                 double *dJ_domega) {
-    (void)T; (void)objective; (void)checkpoint_every; (void)J; (void)dJ_dgz; (void)dJ_domega;
     if (!c) return LBM_EINVAL;
-    return set_err(c, LBM_EUNSUPPORTED, "adjoint not available in this build");
+    if (T < 1) return set_err(c, LBM_EINVAL, "T must be >= 1");
+    if (objective != LBM_J_UBULK && objective != LBM_J_WSS) return set_err(c, LBM_EINVAL, "unknown objective");
+    if (checkpoint_every < 0) return set_err(c, LBM_EINVAL, "checkpoint_every must be >= 0");
+    if (c->hm.size() != 1 || c->wall != LBM_HALFWAY || (c->precision != LBM_F32 && c->precision != LBM_F64) ||
+        c->hm[0].geometry != LBM_PIPE)
+        return set_err(c, LBM_EUNSUPPORTED, "the adjoint needs a single half-way pipe in F32 or F64 storage");
+    const Member &d = c->hm[0];
+    const int64_t K = checkpoint_every > 0 ? std::min<int64_t>(checkpoint_every, T)
+                                           : std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)T)));
+    const int64_t nseg = (T + K - 1) / K;
+    const size_t es = c->precision == LBM_F64 ? 8 : 4;
+    const size_t pop_bytes = (size_t)27 * c->stride * c->esize;
+    const size_t n = (size_t)d.cells;
+    // temporaries: checkpoints, a work copy of the populations, per-step moments of one
+    // segment, two adjoint buffers, FP64 accumulators
+    void *ck = nullptr, *work = nullptr, *mom = nullptr, *lam = nullptr;
+    double *acc = nullptr;
+    cudaError_t e = cudaMalloc(&ck, pop_bytes * nseg);
+    if (e == cudaSuccess) e = cudaMalloc(&work, pop_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&mom, (size_t)K * 9 * n * es);
+    if (e == cudaSuccess) e = cudaMalloc(&lam, 2 * 27 * n * es);
+    const int64_t nblk = (int64_t)((n + 255) / 256);
+    const int64_t nslot = nblk * 8;                  // one slot per warp
+    if (e == cudaSuccess) e = cudaMalloc((void **)&acc, (n + 2 * nslot) * sizeof(double));
+    auto release = [&]() { cudaFree(ck); cudaFree(work); cudaFree(mom); cudaFree(lam); cudaFree(acc); };
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return set_err(c, LBM_ENOMEM, "cannot allocate the adjoint buffers (%lld checkpoints of %zu bytes)",
+                       (long long)nseg, pop_bytes);
+    }
+    // the forward pass runs with direct launches of the default shape, without statistics
+    // or checks; they are restored afterwards
+    double *stats_save = c->stats;
+    const int64_t check_save = c->check_every;
+    const int variant_save = c->variant;
+    const int32_t chunk_save = c->graph_chunk;
+    c->stats = nullptr;
+    c->check_every = 0;
+    c->variant = 0;
+    c->graph_chunk = 0;
+    int rc = LBM_OK;
+    const int64_t t0 = c->t;
+    for (int64_t sgm = 0; sgm < nseg && rc == LBM_OK; ++sgm) {
+        e = cudaMemcpyAsync((char *)ck + sgm * pop_bytes, c->pops, pop_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) { rc = cuda_err(c, e, "checkpoint copy"); break; }
+        const int64_t ns = std::min<int64_t>(K, T - sgm * K);
+        for (int64_t k = 0; k < ns && rc == LBM_OK; ++k) rc = step_direct(c);
+    }
+    const int64_t t_end = c->t;
+    int64_t nfl = d.n_fluid;
+    lbm::AdjArgs j;
+    std::memset(&j, 0, sizeof j);
+    j.objective = objective;
+    j.kappa = 1.0 / ((double)T * (double)std::max<int64_t>(nfl, 1));
+    j.wss = 2.0 / ((double)T * 2.0 * M_PI * d.R * (double)d.nz);
+    j.kappa_f = (float)j.kappa;
+    j.wss_f = (float)j.wss;
+    j.acc = acc;
+    j.blockacc = acc + n;
+    j.nblocks = (int32_t)nblk;
+    if (rc == LBM_OK) {
+        e = cudaMemsetAsync(lam, 0, 2 * 27 * n * es, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, (n + 2 * nslot) * sizeof(double), c->stream);
+        if (e != cudaSuccess) rc = cuda_err(c, e, "adjoint buffer clear");
+    }
+    for (int64_t sgm = nseg - 1; sgm >= 0 && rc == LBM_OK; --sgm) {
+        const int64_t ts = t0 + sgm * K, ns = std::min<int64_t>(K, T - sgm * K);
+        e = cudaMemcpyAsync(work, (char *)ck + sgm * pop_bytes, pop_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) { rc = cuda_err(c, e, "checkpoint restore"); break; }
+        // recompute the segment, storing the moments of every step
+        for (int64_t k = 0; k < ns && rc == LBM_OK; ++k) {
+            StepArgs a = make_args(c, ts + k);
+            a.pops = work;
+            a.moments = (char *)mom + (size_t)k * 9 * n * es;
+            rc = dispatch(c, [&](auto P) {
+                return lbm::launch_step_moments<decltype(P)::value>((int)((ts + k) & 1), a, c->stream);
+            });
+        }
+        // reverse sweep through the segment
+        for (int64_t k = ns - 1; k >= 0 && rc == LBM_OK; --k) {
+            const int64_t t = ts + k;
+            StepArgs a = make_args(c, t);
+            j.lam_next = (char *)lam + (size_t)((t + 1) & 1) * 27 * n * es;
+            j.lam = (char *)lam + (size_t)(t & 1) * 27 * n * es;
+            j.moments = (char *)mom + (size_t)k * 9 * n * es;
+            rc = dispatch(c, [&](auto P) { return lbm::launch_adjoint<decltype(P)::value>(a, j, c->stream); });
+        }
+    }
+    // J and dJ/domega: deterministic sums over cells; dJ/dg_z per cell
+    double host[5] = {0, 0, 0, 0, 0};
+    if (rc == LBM_OK) {
+        double *dout = c->partials + lbm::REDUCE_MAX_BLOCKS * 5;
+        rc = dispatch(c, [&](auto P) {
+            return lbm::launch_sum_columns<decltype(P)::value>(acc + n, nslot, 2, c->partials,
+                                                               lbm::REDUCE_MAX_BLOCKS, dout, c->stream);
+        });
+        if (rc == LBM_OK) {
+            e = cudaMemcpyAsync(host, dout, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess && dJ_dgz)
+                e = cudaMemcpyAsync(dJ_dgz, acc, n * sizeof(double), cudaMemcpyDefault, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) rc = cuda_err(c, e, "adjoint results");
+        }
+    }
+    c->t = t_end;
+    c->stats = stats_save;
+    c->check_every = check_save;
+    c->variant = variant_save;
+    c->graph_chunk = chunk_save;
+    cudaStreamSynchronize(c->stream);
+    release();
+    if (rc) return rc;
+    if (J) *J = host[0];
+    if (dJ_domega) *dJ_domega = host[1];
+    return LBM_OK;
 }
 
 int lbm_profile_enable(lbm_ctx *c, int32_t on) {

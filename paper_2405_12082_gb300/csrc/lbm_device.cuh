@@ -106,6 +106,7 @@ struct Member {
     int64_t t_end;
     const void *gz_field;
     uint32_t nx_mul, nx_shr, ny_mul, ny_shr;   // magic division by nx and ny
+    float gf[3], omegaf;       // float copies of g and omega for the FP32 kernels
     const uint16_t *colmask;   // [ny][nx] in-plane 3x3 fluid mask of every column (device)
     const void *ftab;          // trigger: [3][ny][nx] column factors (P_x, P_y, P_z), compute type
     const void *ztab;          // trigger: [2][nz] cos, sin of kz 2 pi z / L, compute type
@@ -131,6 +132,7 @@ __device__ __forceinline__ uint32_t fastdiv(uint32_t n, uint32_t mul, uint32_t s
 struct StepTime {
     int64_t t;
     double st[LBM_MAX_MEMBERS];
+    float stf[LBM_MAX_MEMBERS];
 };
 
 struct StepArgs {
@@ -143,9 +145,11 @@ struct StepArgs {
     float f16_scale, f16_inv;
     double *stats;            // [4][stride] FP64 accumulators (sample steps)
     double st[LBM_MAX_MEMBERS];      // sin(2 pi t / T) per member (0 when off)
+    float stf[LBM_MAX_MEMBERS];      // the same in float for the FP32 kernels
     int32_t block0[LBM_MAX_MEMBERS + 1];
     const StepTime *times;    // when set, t and st come from times[tidx] (graph replays)
     int32_t tidx;
+    void *moments;            // adjoint recompute: [9][cells] rho, u, s4..s8 of member 0
 };
 
 __device__ __forceinline__ int find_member(const StepArgs &a, int blk) {
@@ -328,19 +332,31 @@ __device__ __forceinline__ void store_pops(const StepArgs &a, const Member &d, c
 // g_x = st cos(2 pi kz z / L) P_x(x, y), g_y = st cos(...) P_y(x, y),
 // g_z = st sin(2 pi kz z / L) P_z(x, y); the column factors (zero outside the radial
 // band) and the z factors are tabulated once per force by k_force_tables.
+// Member parameters in the compute type (no FP64 arithmetic or conversion in FP32 kernels).
+template <class R> __device__ __forceinline__ R g_of(const Member &d, int k) {
+    if constexpr (sizeof(R) == 4) return d.gf[k]; else return d.g[k];
+}
+template <class R> __device__ __forceinline__ R omega_of(const Member &d) {
+    if constexpr (sizeof(R) == 4) return d.omegaf; else return d.omega;
+}
+// sin(2 pi t / T) of member m for this step, in the compute type.
+template <class R> __device__ __forceinline__ R st_of(const StepArgs &a, int m) {
+    if constexpr (sizeof(R) == 4) return a.times ? a.times[a.tidx].stf[m] : a.stf[m];
+    else return a.times ? a.times[a.tidx].st[m] : a.st[m];
+}
+
 template <class R>
-__device__ __forceinline__ void acceleration(const Member &d, const CellPos &p, int64_t t, double st,
+__device__ __forceinline__ void acceleration(const Member &d, const CellPos &p, int64_t t, R st,
                                              R &gx, R &gy, R &gz) {
-    gx = (R)d.g[0];
-    gy = (R)d.g[1];
-    gz = (R)d.g[2];
+    gx = g_of<R>(d, 0);
+    gy = g_of<R>(d, 1);
+    gz = g_of<R>(d, 2);
     if (d.gz_field != nullptr) gz += static_cast<const R *>(d.gz_field)[p.lc];
     if (d.trig && t < d.t_end) {
         const R *ft = static_cast<const R *>(d.ftab);
         const R *zt = static_cast<const R *>(d.ztab);
         const int32_t col = p.y * d.nx + p.x, ncol = d.nx * d.ny;
-        const R s = (R)st;
-        const R sc = s * zt[p.z], ss = s * zt[d.nz + p.z];
+        const R sc = st * zt[p.z], ss = st * zt[d.nz + p.z];
         gx += sc * ft[col];
         gy += sc * ft[ncol + col];
         gz += ss * ft[2 * ncol + col];
@@ -423,8 +439,10 @@ __device__ __forceinline__ void axis_factors(R u, R g, R (&dl)[3], R (&hd)[3]) {
 }
 
 // In-place collision of one fluid cell; v holds f - w on entry and f* - w on exit.
+// With s_out, the five non-equilibrium shear moments s_k = m_k - m_k^eq + R_k / 2
+// (k = 4..8) are returned as well (the adjoint stores them).
 template <class R>
-__device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega) {
+__device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega, R *s_out = nullptr) {
     const Macro<R> mm = macroscopic<R>(v, gx, gy, gz);
     const R rho = mm.rho, ux = mm.ux, uy = mm.uy, uz = mm.uz;
     // raw second moments m4..m8 (the rest weights contribute nothing to them)
@@ -447,11 +465,15 @@ __device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega
     });
     // (1 - omega)(m_k - m_k^eq + R_k / 2), k = 4..8, with the printed m^eq and R
     const R om1 = R(1) - omega;
-    const R a4 = om1 * (m4 - rho * ux * uy + R(0.5) * rho * (gy * ux + gx * uy));
-    const R a5 = om1 * (m5 - rho * ux * uz + R(0.5) * rho * (gz * ux + gx * uz));
-    const R a6 = om1 * (m6 - rho * uy * uz + R(0.5) * rho * (gz * uy + gy * uz));
-    const R a7 = om1 * (m7 - rho * (ux * ux - uy * uy) + rho * (gx * ux - gy * uy));
-    const R a8 = om1 * (m8 - rho * (ux * ux - uz * uz) + rho * (gx * ux - gz * uz));
+    const R s4 = m4 - rho * ux * uy + R(0.5) * rho * (gy * ux + gx * uy);
+    const R s5 = m5 - rho * ux * uz + R(0.5) * rho * (gz * ux + gx * uz);
+    const R s6 = m6 - rho * uy * uz + R(0.5) * rho * (gz * uy + gy * uz);
+    const R s7 = m7 - rho * (ux * ux - uy * uy) + rho * (gx * ux - gy * uy);
+    const R s8 = m8 - rho * (ux * ux - uz * uz) + rho * (gx * ux - gz * uz);
+    if (s_out) {
+        s_out[0] = s4; s_out[1] = s5; s_out[2] = s6; s_out[3] = s7; s_out[4] = s8;
+    }
+    const R a4 = om1 * s4, a5 = om1 * s5, a6 = om1 * s6, a7 = om1 * s7, a8 = om1 * s8;
     const R s12 = (a7 + a8) * R(1.0 / 6.0);
     const R s34 = a8 * R(1.0 / 6.0) - a7 * R(1.0 / 3.0);
     const R s56 = a7 * R(1.0 / 6.0) - a8 * R(1.0 / 3.0);

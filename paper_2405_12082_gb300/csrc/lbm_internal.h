@@ -16,10 +16,11 @@ struct ModesArgs {
 
 // Launch shapes of the step kernel ("variants"): threads per block and the number of
 // resident blocks per SM the register budget is cut for.  FP64 storage has one shape.
+// Shapes 4 and 5 (F32 storage only) are the software-pipelined persistent kernel.
 struct StepShape { int threads, min_blocks; };
-constexpr StepShape STEP_SHAPES[4] = {{256, 4}, {256, 3}, {128, 8}, {512, 2}};
+constexpr StepShape STEP_SHAPES[6] = {{256, 4}, {256, 3}, {128, 8}, {512, 2}, {256, 3}, {128, 6}};
 constexpr StepShape STEP_SHAPE_F64 = {256, 2};
-inline int step_variants(int precision) { return precision == LBM_F64 ? 1 : 4; }
+inline int step_variants(int precision) { return precision == LBM_F64 ? 1 : (precision == LBM_F32 ? 6 : 4); }
 inline int step_threads(int precision, int variant) {
     return precision == LBM_F64 ? STEP_SHAPE_F64.threads : STEP_SHAPES[variant].threads;
 }
@@ -29,6 +30,31 @@ inline int step_threads(int precision, int variant) {
 // step_threads(P, variant) threads.
 template <int P>
 cudaError_t launch_step(int wall, int parity, bool stats, const StepArgs &a, int variant, cudaStream_t s);
+
+// Forward step that also stores rho, u, s4..s8 into a.moments (adjoint recompute;
+// single half-way pipe, F32 or F64 storage, 256-thread blocks).
+template <int P>
+cudaError_t launch_step_moments(int parity, const StepArgs &a, cudaStream_t s);
+
+// One backward step of the adjoint (see k_adjoint).
+struct AdjArgs {
+    const void *lam_next;     // lambda_{t+1}, [27][cells] in the compute type
+    void *lam;                // lambda_t (written)
+    const void *moments;      // [9][cells] of step t: rho, u_x, u_y, u_z, s4..s8
+    double *acc;              // [cells]: dJ/dg_z (accumulated)
+    double *blockacc;         // [2][nblocks * 8]: objective and dJ/domega per warp (accumulated)
+    int32_t objective;        // LBM_J_UBULK | LBM_J_WSS
+    double kappa;             // UBULK: 1 / (T N_fluid)
+    double wss;               // WSS: 2 / (T 2 pi R nz)
+    float kappa_f, wss_f;     // the same in float
+    int32_t nblocks;
+};
+template <int P>
+cudaError_t launch_adjoint(const StepArgs &a, const AdjArgs &j, cudaStream_t s);
+// Deterministic column sums of nv <= 5 double arrays [nv][n] into out[5] (device).
+template <int P>
+cudaError_t launch_sum_columns(const double *base, int64_t n, int nv, double *partials, int n_partials_max,
+                               double *out, cudaStream_t s);
 
 // Per-member kernels: member m of a.members (host copy hm for sizes).
 template <int P>

@@ -10,10 +10,17 @@
 namespace lbm {
 
 // ---- the fused step: load (stream) + wall + force + MRT collision + store ----------------
-// One thread per cell of every member; solid cells return at once.  On sample
-// steps (STATS) u_z^k, k = 1..4, of the pre-collision state is added in FP64.
-// BS threads per block, register budget for MINB resident blocks per SM.
-template <int P, int PAR, int WALL, bool STATS, int BS, int MINB>
+// One thread per cell of every member; solid cells return at once.  EXTRA selects
+// what else the step does: EX_STATS adds u_z^k, k = 1..4, of the pre-collision state to
+// the FP64 sums (sample steps); EX_MOMENTS stores rho, u and s4..s8 of the
+// pre-collision state for the adjoint sweep.  BS threads per block, register budget
+// for MINB resident blocks per SM.
+enum { EX_NONE = 0, EX_STATS = 1, EX_MOMENTS = 2 };
+#ifndef LBM_ADJ_MIN_BLOCKS
+#define LBM_ADJ_MIN_BLOCKS 3
+#endif
+
+template <int P, int PAR, int WALL, int EXTRA, int BS, int MINB>
 __global__ void __launch_bounds__(BS, MINB) k_step(const __grid_constant__ StepArgs a) {
     using R = typename Storage<P>::R;
     const int m = find_member(a, blockIdx.x);
@@ -24,22 +31,165 @@ __global__ void __launch_bounds__(BS, MINB) k_step(const __grid_constant__ StepA
     cell_setup(d, local, p);
     if (!((p.nb >> 4) & 1u)) return;
     const int64_t t = a.times ? a.times[a.tidx].t : a.t;
-    const double stv = a.times ? a.times[a.tidx].st[m] : a.st[m];
+    const R stv = st_of<R>(a, m);
     R v[Q];
     load_pops<P, PAR, WALL>(a, d, p, v);
     R gx, gy, gz;
     acceleration<R>(d, p, t, stv, gx, gy, gz);
-    const Macro<R> mm = collide<R>(v, gx, gy, gz, (R)d.omega);
-    if constexpr (STATS) {
-        const double uz = (double)mm.uz;
-        double *s = a.stats + d.off + p.lc;
-        const double uz2 = uz * uz;
-        s[0] += uz;
-        s[a.stride] += uz2;
-        s[2 * a.stride] += uz2 * uz;
-        s[3 * a.stride] += uz2 * uz2;
+    if constexpr (EXTRA == EX_MOMENTS) {
+        R sk[5];
+        const Macro<R> mm = collide<R>(v, gx, gy, gz, omega_of<R>(d), sk);
+        R *mo = static_cast<R *>(a.moments) + p.lc;
+        const int64_t n = d.cells;
+        mo[0] = mm.rho;
+        mo[n] = mm.ux;
+        mo[2 * n] = mm.uy;
+        mo[3 * n] = mm.uz;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) mo[(4 + k) * n] = sk[k];
+    } else {
+        const Macro<R> mm = collide<R>(v, gx, gy, gz, omega_of<R>(d));
+        if constexpr (EXTRA == EX_STATS) {
+            const double uz = (double)mm.uz;
+            double *s = a.stats + d.off + p.lc;
+            const double uz2 = uz * uz;
+            s[0] += uz;
+            s[a.stride] += uz2;
+            s[2 * a.stride] += uz2 * uz;
+            s[3 * a.stride] += uz2 * uz2;
+        }
     }
     store_pops<P, PAR, WALL>(a, d, p, v);
+}
+
+// ---- software-pipelined persistent step (F32, F64 storage) -----------------------------------
+// A persistent block walks over tiles of BS cells (grid-stride).  Before computing tile k
+// each thread issues the 27 loads of its cell in tile k + 1 as cp.async copies into its
+// own shared-memory column (stage (k+1) mod 2), so the loads of the next tile are in
+// flight while the current one is computed, without holding registers.  Every AA slot is
+// read and written by one cell only within a step, so prefetching ahead of other cells'
+// stores is safe, and each thread reads back only what it copied itself: per-thread
+// cp.async groups replace any block barrier.
+__device__ __forceinline__ void cp_async_4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+extern __shared__ __align__(16) unsigned char lbm_smem[];
+
+template <int P, int PAR, int WALL>
+__device__ __forceinline__ void prefetch_pops(const StepArgs &a, const Member &d, const CellPos &p, uint32_t sbase,
+                                              int stride_bytes) {
+    using T = typename Storage<P>::T;
+    const T *base = static_cast<const T *>(a.pops) + d.off;
+    const uint32_t st = (uint32_t)a.stride;
+    const uint32_t lc = (uint32_t)p.lc;
+    sfor<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int ib = opp_of(i);
+        uint32_t idx;
+        if constexpr (PAR == 0) {
+            idx = i * st + lc;
+        } else {
+            const uint32_t pull = ib * st + (uint32_t)(p.lc + src_offset<i>(p));
+            if constexpr (WALL == LBM_FULLWAY || (cx_of(i) == 0 && cy_of(i) == 0)) idx = pull;
+            else idx = src_is_fluid<i>(p) ? pull : i * st + lc;
+        }
+        if constexpr (sizeof(T) == 8) cp_async_8(sbase + i * stride_bytes, base + idx);
+        else cp_async_4(sbase + i * stride_bytes, base + idx);
+    });
+}
+
+struct TileCell {
+    int m;
+    bool active;
+    CellPos p;
+};
+
+template <int BS>
+__device__ __forceinline__ TileCell tile_cell(const StepArgs &a, int tile) {
+    TileCell c;
+    c.m = 0;
+    c.active = false;
+    if (tile < a.nblocks_total) {
+        c.m = find_member(a, tile);
+        const Member &d = a.members[c.m];
+        const uint32_t local = (uint32_t)(tile - a.block0[c.m]) * BS + threadIdx.x;
+        if (local < (uint32_t)d.cells) {
+            cell_setup(d, local, c.p);
+            c.active = (c.p.nb >> 4) & 1u;
+        }
+    }
+    return c;
+}
+
+template <int P, int PAR, int WALL, int EXTRA, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_step_pipe(const __grid_constant__ StepArgs a) {
+    using S = Storage<P>;
+    using T = typename S::T;
+    using R = typename S::R;
+    const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(lbm_smem);
+    const int stride_bytes = BS * (int)sizeof(T);            // one population column of a stage
+    const uint32_t stage_bytes = (uint32_t)(Q * BS * sizeof(T));
+    const uint32_t mine = smem0 + threadIdx.x * sizeof(T);
+    const T *smem_t = reinterpret_cast<const T *>(lbm_smem) + threadIdx.x;
+    int tile = blockIdx.x;
+    TileCell cur = tile_cell<BS>(a, tile);
+    if (cur.active) prefetch_pops<P, PAR, WALL>(a, a.members[cur.m], cur.p, mine, stride_bytes);
+    cp_async_commit();
+    const int64_t t = a.times ? a.times[a.tidx].t : a.t;
+    for (int k = 0; tile < a.nblocks_total; ++k) {
+        const int next_tile = tile + gridDim.x;
+        TileCell nxt = tile_cell<BS>(a, next_tile);
+        if (nxt.active)
+            prefetch_pops<P, PAR, WALL>(a, a.members[nxt.m], nxt.p, mine + ((k + 1) & 1) * stage_bytes, stride_bytes);
+        cp_async_commit();
+        cp_async_wait_one();                                 // this thread's copies of tile k are done
+        if (cur.active) {
+            const Member &d = a.members[cur.m];
+            const T *col = smem_t + (k & 1) * (Q * BS);
+            R v[Q];
+            const R inv = (R)a.f16_inv;
+            sfor<0, Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                v[i] = S::ld(col + i * BS, inv);
+            });
+            if constexpr (WALL == LBM_BOUZIDI) {
+                if (cur.p.nb != 0x1FFu) {
+                    sfor<0, Q>([&](auto jc) {
+                        constexpr int j = decltype(jc)::value;
+                        if constexpr (cx_of(j) != 0 || cy_of(j) != 0) {
+                            if (!dst_is_fluid<j>(cur.p)) {
+                                BLink<R> b = bouzidi_link<R, j>(d, cur.p);
+                                v[opp_of(j)] += b.C * v[j];
+                            }
+                        }
+                    });
+                }
+            }
+            R gx, gy, gz;
+            acceleration<R>(d, cur.p, t, st_of<R>(a, cur.m), gx, gy, gz);
+            const Macro<R> mm = collide<R>(v, gx, gy, gz, omega_of<R>(d));
+            if constexpr (EXTRA == EX_STATS) {
+                const double uz = (double)mm.uz;
+                double *sp = a.stats + d.off + cur.p.lc;
+                const double uz2 = uz * uz;
+                sp[0] += uz;
+                sp[a.stride] += uz2;
+                sp[2 * a.stride] += uz2 * uz;
+                sp[3 * a.stride] += uz2 * uz2;
+            }
+            store_pops<P, PAR, WALL>(a, d, cur.p, v);
+        }
+        tile = next_tile;
+        cur = nxt;
+    }
+    cp_async_wait_all();
 }
 
 // ---- state I/O: the exact inverse of load_pops ---------------------------------------------
@@ -119,7 +269,7 @@ __global__ void k_moments(const __grid_constant__ StepArgs a, int m, typename St
     R v[Q];
     load_pops<P, PAR, WALL>(a, d, p, v);
     R gx, gy, gz;
-    acceleration<R>(d, p, a.t, a.st[m], gx, gy, gz);
+    acceleration<R>(d, p, a.t, st_of<R>(a, m), gx, gy, gz);
     const Macro<R> mm = macroscopic<R>(v, gx, gy, gz);
     rho[local] = mm.rho;
     u[local] = mm.ux;
@@ -308,7 +458,7 @@ __device__ double uz_at(const StepArgs &a, const Member &d, int m, int x, int y,
     R v[Q];
     load_pops<P, PAR, WALL>(a, d, p, v);
     R gx, gy, gz;
-    acceleration<R>(d, p, a.t, a.st[m], gx, gy, gz);
+    acceleration<R>(d, p, a.t, st_of<R>(a, m), gx, gy, gz);
     return (double)macroscopic<R>(v, gx, gy, gz).uz;
 }
 
@@ -377,6 +527,217 @@ __global__ void k_force_tables(const Member *members, int m, R *ftab, R *ztab) {
     }
 }
 
+// ---- adjoint step ------------------------------------------------------------------------------
+// Reverse of step t of a single half-way pipe.  mu = S^T lambda_{t+1} gathers
+// lambda_i(x + c_i) when x + c_i is fluid and lambda_ibar(x) across a wall link (the
+// transpose of half-way bounce-back); the wall-shear objective adds 2 c_iz / (T A_w) on
+// wall links.  The collision is a function of rho, u and the raw shear moments m4..m8:
+//   f*_j = w_j (rho P_j - 1) + (rho / 2) w_j g . grad_u P_j + (1 - omega) sum_k C_kj s_k,
+//   P_j = psi(c_jx, u_x) psi(c_jy, u_y) psi(c_jz, u_z) (normalised), s_k = m_k - rho e_k(u)
+//   + rho r_k(u, g) / 2,
+// so lambda_t,i = A_rho + sum_a A_ua (c_ia - v_a) / rho + (1 - omega) sum_k q_k M_k(c_i)
+// with v = u - g / 2, q_k = sum_j mu_j C_kj and A_rho, A_u the partial derivatives of
+// sum_j mu_j f*_j.  The sums over j of mu_j w_j times products of psi and its first two
+// u-derivatives are contracted axis by axis (z, then y, then x).  Per cell the FP64
+// accumulators collect the objective, dJ/dg_z(x) and dJ/domega.
+template <int P, int OBJ>
+__device__ __forceinline__ void adjoint_cell(const StepArgs &a, const AdjArgs &j, const Member &d, const CellPos &p,
+                                             typename Storage<P>::R &jterm, typename Storage<P>::R &wterm) {
+    using R = typename Storage<P>::R;
+    const uint32_t n = (uint32_t)d.cells, lc = (uint32_t)p.lc;
+    const R *M = static_cast<const R *>(j.moments) + lc;
+    const R rho = M[0], ux = M[n], uy = M[2 * n], uz = M[3 * n];
+    const R s4 = M[4 * n], s5 = M[5 * n], s6 = M[6 * n], s7 = M[7 * n], s8 = M[8 * n];
+    R gx, gy, gz;
+    acceleration<R>(d, p, a.t, st_of<R>(a, 0), gx, gy, gz);
+    const R om1 = R(1) - omega_of<R>(d);
+    const R half = R(0.5);
+
+    // mu = S^T lambda_{t+1} (+ wall shear source)
+    const R wss = sizeof(R) == 4 ? (R)j.wss_f : (R)j.wss;
+    const R *ln = static_cast<const R *>(j.lam_next);
+    R mu[Q];
+    sfor<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int ib = opp_of(i);
+        const uint32_t push = i * n + (uint32_t)(p.lc + nb_offset<i>(p));
+        if constexpr (cx_of(i) == 0 && cy_of(i) == 0) {
+            mu[i] = ln[push];
+        } else {
+            const bool f = dst_is_fluid<i>(p);
+            mu[i] = ln[f ? push : ib * n + lc];
+            if constexpr (OBJ == LBM_J_WSS && cz_of(i) != 0)
+                if (!f) mu[i] += wss * R(cz_of(i));
+        }
+    });
+
+    // axis factors psi, psi', psi'' at c = -1, 0, +1
+    R X0[3], X1[3], Y0[3], Y1[3], Z0[3], Z1[3];
+    auto fac = [&](R u, R (&F0)[3], R (&F1)[3]) {
+        const R u2 = u * u;
+        F0[1] = R(1) - R(1.5) * u2;
+        F0[0] = R(1) - R(3) * u + R(3) * u2;
+        F0[2] = R(1) + R(3) * u + R(3) * u2;
+        F1[1] = R(-3) * u;
+        F1[0] = R(-3) + R(6) * u;
+        F1[2] = R(3) + R(6) * u;
+    };
+    fac(ux, X0, X1);
+    fac(uy, Y0, Y1);
+    fac(uz, Z0, Z1);
+    const R D2[3] = {R(6), R(-3), R(6)};   // psi'' (same on every axis)
+
+    // contraction over z: T0/T1/T2[a][b] = sum_c mu w Z0/Z1/Z2
+    R T0[3][3], T1[3][3], T2[3][3];
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) T0[aa][bb] = T1[aa][bb] = T2[aa][bb] = R(0);
+    sfor<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int aa = cx_of(i) + 1, bb = cy_of(i) + 1, cc = cz_of(i) + 1;
+        const R mw = mu[i] * R(w_of(i));
+        T0[aa][bb] += mw * Z0[cc];
+        T1[aa][bb] += mw * Z1[cc];
+        T2[aa][bb] += mw * D2[cc];
+    });
+    // over y
+    R Y00[3], Y01[3], Y02[3], Y10[3], Y11[3], Y20[3];
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) {
+        Y00[aa] = Y01[aa] = Y02[aa] = Y10[aa] = Y11[aa] = Y20[aa] = R(0);
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+            Y00[aa] += Y0[bb] * T0[aa][bb];
+            Y01[aa] += Y0[bb] * T1[aa][bb];
+            Y02[aa] += Y0[bb] * T2[aa][bb];
+            Y10[aa] += Y1[bb] * T0[aa][bb];
+            Y11[aa] += Y1[bb] * T1[aa][bb];
+            Y20[aa] += D2[bb] * T0[aa][bb];
+        }
+    }
+    // over x
+    R K000 = 0, K001 = 0, K002 = 0, K010 = 0, K011 = 0, K020 = 0, K100 = 0, K101 = 0, K110 = 0, K200 = 0;
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) {
+        K000 += X0[aa] * Y00[aa];
+        K001 += X0[aa] * Y01[aa];
+        K002 += X0[aa] * Y02[aa];
+        K010 += X0[aa] * Y10[aa];
+        K011 += X0[aa] * Y11[aa];
+        K020 += X0[aa] * Y20[aa];
+        K100 += X1[aa] * Y00[aa];
+        K101 += X1[aa] * Y01[aa];
+        K110 += X1[aa] * Y10[aa];
+        K200 += D2[aa] * Y00[aa];
+    }
+    // q_k = sum_j mu_j C_kj (columns of (M^T)^{-1})
+    const R q4 = R(0.25) * (mu[7] + mu[10] - mu[8] - mu[9]);
+    const R q5 = R(0.25) * (mu[11] + mu[14] - mu[12] - mu[13]);
+    const R q6 = R(0.25) * (mu[15] + mu[18] - mu[16] - mu[17]);
+    const R q7 = (mu[1] + mu[2] + mu[5] + mu[6]) * R(1.0 / 6.0) - (mu[3] + mu[4]) * R(1.0 / 3.0);
+    const R q8 = (mu[1] + mu[2] + mu[3] + mu[4]) * R(1.0 / 6.0) - (mu[5] + mu[6]) * R(1.0 / 3.0);
+
+    const R Arho = K000 + half * (gx * K100 + gy * K010 + gz * K001) +
+                   om1 * (q4 * (-ux * uy + half * (gy * ux + gx * uy)) + q5 * (-ux * uz + half * (gz * ux + gx * uz)) +
+                          q6 * (-uy * uz + half * (gz * uy + gy * uz)) + q7 * (-(ux * ux - uy * uy) + (gx * ux - gy * uy)) +
+                          q8 * (-(ux * ux - uz * uz) + (gx * ux - gz * uz)));
+    const R Aux = rho * (K100 + half * (gx * K200 + gy * K110 + gz * K101) +
+                         om1 * (q4 * (-uy + half * gy) + q5 * (-uz + half * gz) + (q7 + q8) * (R(-2) * ux + gx)));
+    const R Auy = rho * (K010 + half * (gx * K110 + gy * K020 + gz * K011) +
+                         om1 * (q4 * (-ux + half * gx) + q6 * (-uz + half * gz) + q7 * (R(2) * uy - gy)));
+    const R Auz = rho * (K001 + half * (gx * K101 + gy * K011 + gz * K002) +
+                         om1 * (q5 * (-ux + half * gx) + q6 * (-uy + half * gy) + q8 * (R(2) * uz - gz)));
+    const R irho = R(1) / rho;
+    const R kap = sizeof(R) == 4 ? (R)j.kappa_f : (R)j.kappa;
+    const R Bx = Aux * irho, By = Auy * irho;
+    const R Bz = Auz * irho + (OBJ == LBM_J_UBULK ? kap * irho : R(0));
+    const R vx = ux - half * gx, vy = uy - half * gy, vz = uz - half * gz;
+    const R base = Arho - (Bx * vx + By * vy + Bz * vz);
+
+    R *lo = static_cast<R *>(j.lam);
+    sfor<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+        R l = base + R(cx) * Bx + R(cy) * By + R(cz) * Bz;
+        l += om1 * (R(cx * cy) * q4 + R(cx * cz) * q5 + R(cy * cz) * q6 + R(cx * cx - cy * cy) * q7 +
+                    R(cx * cx - cz * cz) * q8);
+        lo[i * n + lc] = l;
+    });
+
+    // accumulators: objective, dJ/dg_z, dJ/domega
+    jterm = R(0);
+    if constexpr (OBJ == LBM_J_UBULK) {
+        jterm = kap * uz;
+    } else {
+        if (p.nb != 0x1FFu) {
+            sfor<0, Q>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+                if constexpr (cz != 0 && (cx != 0 || cy != 0)) {
+                    if (!dst_is_fluid<i>(p)) {
+                        const R Pi = X0[cx + 1] * Y0[cy + 1] * Z0[cz + 1];
+                        const R Gi = gx * X1[cx + 1] * Y0[cy + 1] * Z0[cz + 1] + gy * X0[cx + 1] * Y1[cy + 1] * Z0[cz + 1] +
+                                     gz * X0[cx + 1] * Y0[cy + 1] * Z1[cz + 1];
+                        R shear = 0;
+                        if constexpr (cy == 0) shear = R(cx * cz) * R(0.25) * s5;
+                        if constexpr (cx == 0) shear = R(cy * cz) * R(0.25) * s6;
+                        const R fstar = R(w_of(i)) * rho * (Pi + half * Gi) + om1 * shear;
+                        jterm += wss * R(cz) * fstar;
+                    }
+                }
+            });
+        }
+    }
+    const R gterm = half * rho * K001 + om1 * half * rho * (q5 * ux + q6 * uy - R(2) * q8 * uz) + half * Auz +
+                    (OBJ == LBM_J_UBULK ? half * kap : R(0));
+    wterm = -(q4 * s4 + q5 * s5 + q6 * s6 + q7 * s7 + q8 * s8);
+    j.acc[lc] += (double)gterm;
+}
+
+// One thread per cell; the objective and dJ/domega terms are summed per block in a fixed
+// order and added to the block's own FP64 slots (deterministic), dJ/dg_z per cell.
+template <int P, int OBJ>
+__global__ void __launch_bounds__(256, LBM_ADJ_MIN_BLOCKS) k_adjoint(const __grid_constant__ StepArgs a,
+                                                                     const AdjArgs j) {
+    using R = typename Storage<P>::R;
+    const Member &d = a.members[0];
+    const int64_t local = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    R x0 = 0, x1 = 0;
+    if (local < d.cells) {
+        CellPos p;
+        cell_setup(d, (uint32_t)local, p);
+        if ((p.nb >> 4) & 1u) adjoint_cell<P, OBJ>(a, j, d, p, x0, x1);
+    }
+    // warp sums of the objective and omega terms in the compute type, added to the
+    // warp's own FP64 slots (fixed order, no block barrier)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x0 += __shfl_down_sync(0xFFFFFFFFu, x0, o);
+        x1 += __shfl_down_sync(0xFFFFFFFFu, x1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        const int64_t wslot = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+        j.blockacc[wslot] += (double)x0;
+        j.blockacc[(int64_t)j.nblocks * 8 + wslot] += (double)x1;
+    }
+}
+
+// Column sums of up to five double arrays (stride n) into per-block partials.
+static __global__ void __launch_bounds__(REDUCE_BLOCK) k_sum_columns(const double *base, int64_t n, int nv,
+                                                                 double *partials) {
+    __shared__ double sh[5 * 32];
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            if (k < nv) acc[k] += base[k * n + i];
+    block_sum<5>(acc, sh);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) partials[blockIdx.x * 5 + k] = acc[k];
+}
+
 // ---- host launchers ------------------------------------------------------------------------------
 #define LBM_DISPATCH_WP(WALL_, PAR_, ...)                                          \
     do {                                                                          \
@@ -397,8 +758,33 @@ static inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b -
 template <int P, int BS, int MINB>
 cudaError_t launch_step_shape(int wall, int parity, bool stats, const StepArgs &a, cudaStream_t s) {
     LBM_DISPATCH_WP(wall, parity, {
-        if (stats) k_step<P, PA, W, true, BS, MINB><<<a.nblocks_total, BS, 0, s>>>(a);
-        else k_step<P, PA, W, false, BS, MINB><<<a.nblocks_total, BS, 0, s>>>(a);
+        if (stats) k_step<P, PA, W, EX_STATS, BS, MINB><<<a.nblocks_total, BS, 0, s>>>(a);
+        else k_step<P, PA, W, EX_NONE, BS, MINB><<<a.nblocks_total, BS, 0, s>>>(a);
+    });
+    return cudaGetLastError();
+}
+
+template <int P, int BS, int MINB>
+cudaError_t launch_step_pipe(int wall, int parity, bool stats, const StepArgs &a, cudaStream_t s) {
+    using T = typename Storage<P>::T;
+    const size_t smem = 2 * (size_t)Q * BS * sizeof(T);
+    static int grid_cache[2][3][2] = {};            // resident blocks x SMs, per (parity, wall, stats)
+    int &grid = grid_cache[parity][wall][stats ? 1 : 0];
+    cudaError_t e = cudaSuccess;
+    LBM_DISPATCH_WP(wall, parity, {
+        auto kern = stats ? k_step_pipe<P, PA, W, EX_STATS, BS, MINB> : k_step_pipe<P, PA, W, EX_NONE, BS, MINB>;
+        if (grid == 0) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0, dev = 0, sms = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BS, smem);
+            if (e == cudaSuccess) e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            grid = std::max(1, per_sm) * std::max(1, sms);
+        }
+        const int g = std::min(grid, a.nblocks_total);
+        kern<<<g, BS, smem, s>>>(a);
     });
     return cudaGetLastError();
 }
@@ -413,8 +799,51 @@ cudaError_t launch_step(int wall, int parity, bool stats, const StepArgs &a, int
             case 1: return launch_step_shape<P, 256, 3>(wall, parity, stats, a, s);
             case 2: return launch_step_shape<P, 128, 8>(wall, parity, stats, a, s);
             case 3: return launch_step_shape<P, 512, 2>(wall, parity, stats, a, s);
+            case 4:
+                if constexpr (P == LBM_F32) return launch_step_pipe<P, 256, 3>(wall, parity, stats, a, s);
+                else return cudaErrorInvalidValue;
+            case 5:
+                if constexpr (P == LBM_F32) return launch_step_pipe<P, 128, 6>(wall, parity, stats, a, s);
+                else return cudaErrorInvalidValue;
             default: return launch_step_shape<P, 256, 4>(wall, parity, stats, a, s);
         }
+    }
+}
+
+// Forward step of a single half-way pipe that also stores the adjoint moments (F32, F64).
+template <int P>
+cudaError_t launch_step_moments(int parity, const StepArgs &a, cudaStream_t s) {
+    if constexpr (P == LBM_F64 || P == LBM_F32) {
+        constexpr int BS = 256, MINB = (P == LBM_F64) ? 2 : 4;
+        if (parity == 0) k_step<P, 0, LBM_HALFWAY, EX_MOMENTS, BS, MINB><<<a.nblocks_total, BS, 0, s>>>(a);
+        else k_step<P, 1, LBM_HALFWAY, EX_MOMENTS, BS, MINB><<<a.nblocks_total, BS, 0, s>>>(a);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
+template <int P>
+cudaError_t launch_sum_columns(const double *base, int64_t n, int nv, double *partials, int n_partials_max,
+                               double *out, cudaStream_t s) {
+    int nb = (int)blocks_for(n, REDUCE_BLOCK);
+    if (nb > n_partials_max) nb = n_partials_max;
+    if (nb < 1) nb = 1;
+    k_sum_columns<<<nb, REDUCE_BLOCK, 0, s>>>(base, n, nv, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_final<<<1, REDUCE_BLOCK, 0, s>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_adjoint(const StepArgs &a, const AdjArgs &j, cudaStream_t s) {
+    if constexpr (P == LBM_F64 || P == LBM_F32) {
+        if (j.objective == LBM_J_UBULK) k_adjoint<P, LBM_J_UBULK><<<j.nblocks, 256, 0, s>>>(a, j);
+        else k_adjoint<P, LBM_J_WSS><<<j.nblocks, 256, 0, s>>>(a, j);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
     }
 }
 
@@ -500,6 +929,10 @@ cudaError_t launch_modes(int wall, int parity, const StepArgs &a, const Member &
 #define LBM_INSTANTIATE(P)                                                                              \
     namespace lbm {                                                                                     \
     template cudaError_t launch_step<P>(int, int, bool, const StepArgs &, int, cudaStream_t);           \
+    template cudaError_t launch_step_moments<P>(int, const StepArgs &, cudaStream_t);                    \
+    template cudaError_t launch_adjoint<P>(const StepArgs &, const AdjArgs &, cudaStream_t);             \
+    template cudaError_t launch_sum_columns<P>(const double *, int64_t, int, double *, int, double *,    \
+                                               cudaStream_t);                                            \
     template cudaError_t launch_moments<P>(int, int, const StepArgs &, const Member &, int, void *,     \
                                            void *, cudaStream_t);                                       \
     template cudaError_t launch_get_pops<P>(int, int, const StepArgs &, const Member &, int, double *,  \
