@@ -23,7 +23,10 @@ struct lbm_ctx {
     Member *dm = nullptr;            // device copies
     int sel = 0;
     void *pops = nullptr;
-    int64_t stride = 0;              // cells per population plane
+    int64_t stride = 0;              // stored cells per population plane (all members)
+    int64_t dense_total = 0;         // cells of all members in dense per-cell arrays
+    std::vector<std::vector<int32_t>> rows;      // compact layout: rowbase[ny] ++ rowx0[ny] per member
+    std::vector<std::vector<uint16_t>> rowof;    // compact layout: row of each stored position
     size_t esize = 0;                // bytes per stored population
     int64_t t = 0;
     float f16_scale = 1.f, f16_inv = 1.f;
@@ -103,11 +106,13 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 // trigger-force factors.  Allocated once; the force tables are refilled by set_force.
 int build_tables(lbm_ctx *c) {
     const size_t es = c->precision == LBM_F64 ? 8 : 4;
-    std::vector<size_t> at(c->hm.size() * 3);
+    std::vector<size_t> at(c->hm.size() * 3), at_rows(c->hm.size());
     size_t total = 0;
     for (size_t m = 0; m < c->hm.size(); ++m) {
         const Member &d = c->hm[m];
         const size_t ncol = (size_t)d.nx * d.ny;
+        at_rows[m] = total;
+        if (d.compact) total += align256(c->rows[m].size() * 4) + align256(c->rowof[m].size() * 2);
         at[3 * m] = total; total += align256(ncol * 2);
         at[3 * m + 1] = total; total += align256(3 * ncol * es);
         at[3 * m + 2] = total; total += align256(2 * (size_t)d.nz * es);
@@ -133,10 +138,29 @@ int build_tables(lbm_ctx *c) {
         char *g = (char *)c->geo;
         LBM_CUDA(c, cudaMemcpy(g + at[3 * m], mask.data(), mask.size() * 2, cudaMemcpyHostToDevice));
         d.colmask = (const uint16_t *)(g + at[3 * m]);
+        if (d.compact) {
+            const size_t rb = c->rows[m].size() * 4;
+            LBM_CUDA(c, cudaMemcpy(g + at_rows[m], c->rows[m].data(), rb, cudaMemcpyHostToDevice));
+            LBM_CUDA(c, cudaMemcpy(g + at_rows[m] + align256(rb), c->rowof[m].data(), c->rowof[m].size() * 2,
+                                   cudaMemcpyHostToDevice));
+            d.rowbase = (const int32_t *)(g + at_rows[m]);
+            d.rowx0 = d.rowbase + d.ny;
+            d.rowof = (const uint16_t *)(g + at_rows[m] + align256(rb));
+        }
         d.ftab = g + at[3 * m + 1];
         d.ztab = g + at[3 * m + 2];
     }
     return LBM_OK;
+}
+
+size_t esize_of(int p) {
+    switch (p) {
+        case LBM_F64: return 8;
+        case LBM_F32: return 4;
+        case LBM_F16S: return 2;
+        case LBM_BF16: return 2;
+    }
+    return 0;
 }
 
 int check_force(lbm_ctx *c, const lbm_force *f) {
@@ -180,7 +204,8 @@ void fill_force(Member &d, const lbm_force *f) {
     d.gz_field = f ? f->gz_field : nullptr;
 }
 
-int build_member(lbm_ctx *c, const lbm_grid *g, const lbm_relax *r, const lbm_force *f, Member &d) {
+int build_member(lbm_ctx *c, const lbm_grid *g, const lbm_relax *r, const lbm_force *f, Member &d,
+                 std::vector<int32_t> *rows = nullptr, std::vector<uint16_t> *rowof = nullptr) {
     if (!g || !r) return set_err(c, LBM_EINVAL, "grid and relax must not be NULL");
     if (g->nx < 1 || g->ny < 1 || g->nz < 1) return set_err(c, LBM_EINVAL, "grid sizes must be >= 1");
     const int64_t cells = (int64_t)g->nx * g->ny * g->nz;
@@ -213,18 +238,38 @@ int build_member(lbm_ctx *c, const lbm_grid *g, const lbm_relax *r, const lbm_fo
     fill_force(d, f);
     lbm::fastdiv_setup((uint32_t)g->nx, d.nx_mul, d.nx_shr);
     lbm::fastdiv_setup((uint32_t)g->ny, d.ny_mul, d.ny_shr);
+    // storage layout: compact fluid rows for pipes whose walls never touch solid cells
+    d.compact = (g->geometry == LBM_PIPE && g->wall != LBM_FULLWAY && rows && rowof) ? 1 : 0;
+    d.scells = d.cells;
+    d.Ps = d.nx * d.ny;
+    if (d.compact) {
+        const int pad = (int)(64 / esize_of(g->precision));      // elements per 64 bytes
+        rows->assign(2 * (size_t)g->ny, 0);
+        int64_t ps = 0;
+        for (int y = 0; y < g->ny; ++y) {
+            int x0 = -1, x1 = -1;
+            for (int x = 0; x < g->nx; ++x)
+                if (col_fluid_host(d, x, y)) {
+                    if (x0 < 0) x0 = x;
+                    x1 = x;
+                }
+            (*rows)[y] = (int32_t)ps;
+            (*rows)[g->ny + y] = x0 < 0 ? 0 : x0;
+            if (x0 >= 0) ps += ((int64_t)(x1 - x0 + 1) + pad - 1) / pad * pad;
+        }
+        if (ps * g->nz >= (1ll << 31) || ps >= 0xFFFF * 64)
+            return set_err(c, LBM_EINVAL, "pipe too large for the compact layout");
+        rowof->assign((size_t)ps, 0xFFFF);
+        for (int y = 0; y < g->ny; ++y)
+            for (int x = 0; x < g->nx; ++x)
+                if (col_fluid_host(d, x, y)) (*rowof)[(*rows)[y] + (x - (*rows)[g->ny + y])] = (uint16_t)y;
+        d.Ps = (int32_t)ps;
+        d.scells = ps * g->nz;
+    }
+    lbm::fastdiv_setup((uint32_t)std::max<int32_t>(d.Ps, 1), d.ps_mul, d.ps_shr);
     return LBM_OK;
 }
 
-size_t esize_of(int p) {
-    switch (p) {
-        case LBM_F64: return 8;
-        case LBM_F32: return 4;
-        case LBM_F16S: return 2;
-        case LBM_BF16: return 2;
-    }
-    return 0;
-}
 
 StepArgs make_args(const lbm_ctx *c, int64_t t) {
     StepArgs a;
@@ -237,6 +282,7 @@ StepArgs make_args(const lbm_ctx *c, int64_t t) {
     a.f16_scale = c->f16_scale;
     a.f16_inv = c->f16_inv;
     a.stats = c->stats;
+    a.dstride = c->dense_total;
     const int bs = lbm::step_threads(c->precision, c->variant);
     int64_t blk = 0;
     for (size_t m = 0; m < c->hm.size(); ++m) {
@@ -244,7 +290,7 @@ StepArgs make_args(const lbm_ctx *c, int64_t t) {
         a.st[m] = (d.trig && t < d.t_end) ? std::sin(2.0 * M_PI * (double)t / d.period) : 0.0;
         a.stf[m] = (float)a.st[m];
         a.block0[m] = (int32_t)blk;
-        blk += (d.cells + bs - 1) / bs;
+        blk += (d.scells + bs - 1) / bs;
     }
     a.block0[c->hm.size()] = (int32_t)blk;
     a.nblocks_total = (int32_t)blk;
@@ -304,21 +350,27 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
     lbm_ctx *c = new lbm_ctx();
     c->precision = prec;
     c->wall = wall;
+    c->variant = prec == LBM_F64 ? 0 : 2;   // 128 x 8: the fastest shape in sweeps on GB300
     c->stream = (cudaStream_t)stream;
     c->f16_scale = std::ldexp(1.0f, s16);
     c->f16_inv = std::ldexp(1.0f, -s16);
     c->hm.resize(n);
-    int64_t off = 0, blk = 0;
+    int64_t off = 0, blk = 0, doff = 0;
     for (int k = 0; k < n; ++k) {
         if (grids[k].precision != prec || grids[k].wall != wall) {
             delete c;
             return set_err(nullptr, LBM_EINVAL, "all members must share precision and wall");
         }
-        int rc = build_member(nullptr, &grids[k], &relax[k], force ? &force[k] : nullptr, c->hm[k]);
+        c->rows.emplace_back();
+        c->rowof.emplace_back();
+        int rc = build_member(nullptr, &grids[k], &relax[k], force ? &force[k] : nullptr, c->hm[k], &c->rows.back(),
+                              &c->rowof.back());
         if (rc) { delete c; return rc; }
         c->hm[k].off = off;
-        off += ceil_div(c->hm[k].cells, 64) * 64;   // keep every member 64-cell aligned
-        blk += ceil_div(c->hm[k].cells, 128);        // the smallest launch shape
+        off += ceil_div(c->hm[k].scells, 64) * 64;   // keep every member 64-cell aligned
+        c->hm[k].doff = doff;
+        doff += ceil_div(c->hm[k].cells, 64) * 64;
+        blk += ceil_div(c->hm[k].scells, 128);       // the smallest launch shape
         c->grids.push_back(grids[k]);
         lbm_force fz;
         std::memset(&fz, 0, sizeof fz);
@@ -331,6 +383,7 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
                        "27 x %lld cells exceed the 32-bit population index of the step kernels", (long long)off);
     }
     c->stride = off;
+    c->dense_total = doff;
     c->esize = esize_of(prec);
     c->mass0.assign(n, 0.0);
     c->mass0_valid.assign(n, false);
@@ -545,7 +598,7 @@ int lbm_init(lbm_ctx *c, int32_t profile, double noise_amp, uint64_t seed) {
         c->mass0_valid[m] = false;
     }
     if (c->stats) {
-        LBM_CUDA(c, cudaMemsetAsync(c->stats, 0, sizeof(double) * 4 * c->stride, c->stream));
+        LBM_CUDA(c, cudaMemsetAsync(c->stats, 0, sizeof(double) * 4 * c->dense_total, c->stream));
         c->stats_count = 0;
     }
     return LBM_OK;
@@ -924,14 +977,14 @@ int lbm_stats_enable(lbm_ctx *c, int32_t every) {
     if (!c) return LBM_EINVAL;
     if (every < 1) return set_err(c, LBM_EINVAL, "stats interval must be >= 1");
     if (!c->stats) {
-        cudaError_t e = cudaMalloc((void **)&c->stats, sizeof(double) * 4 * c->stride);
+        cudaError_t e = cudaMalloc((void **)&c->stats, sizeof(double) * 4 * c->dense_total);
         if (e != cudaSuccess) {
             cudaGetLastError();
             c->stats = nullptr;
             return set_err(c, LBM_ENOMEM, "cannot allocate statistics accumulators");
         }
     }
-    LBM_CUDA(c, cudaMemsetAsync(c->stats, 0, sizeof(double) * 4 * c->stride, c->stream));
+    LBM_CUDA(c, cudaMemsetAsync(c->stats, 0, sizeof(double) * 4 * c->dense_total, c->stream));
     c->stats_every = every;
     c->stats_count = 0;
     return LBM_OK;
@@ -941,8 +994,8 @@ int lbm_stats_get(lbm_ctx *c, double *acc, int64_t *count) {
     if (!c || !acc) return LBM_EINVAL;
     if (!c->stats) return set_err(c, LBM_EINVAL, "statistics are not enabled");
     const Member &d = c->hm[c->sel];
-    LBM_CUDA(c, cudaMemcpy2DAsync(acc, (size_t)d.cells * sizeof(double), c->stats + d.off,
-                                  (size_t)c->stride * sizeof(double), (size_t)d.cells * sizeof(double), 4,
+    LBM_CUDA(c, cudaMemcpy2DAsync(acc, (size_t)d.cells * sizeof(double), c->stats + d.doff,
+                                  (size_t)c->dense_total * sizeof(double), (size_t)d.cells * sizeof(double), 4,
                                   cudaMemcpyDefault, c->stream));
     if (!is_device_ptr(acc)) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     if (count) *count = c->stats_count;
@@ -1005,7 +1058,8 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     const int64_t nseg = (T + K - 1) / K;
     const size_t es = c->precision == LBM_F64 ? 8 : 4;
     const size_t pop_bytes = (size_t)27 * c->stride * c->esize;
-    const size_t n = (size_t)d.cells;
+    const size_t n = (size_t)d.scells;       // stored cells (adjoint and moment buffers)
+    const size_t nd = (size_t)d.cells;       // dense cells (dJ/dg_z)
     // temporaries: checkpoints, a work copy of the populations, per-step moments of one
     // segment, two adjoint buffers, FP64 accumulators
     void *ck = nullptr, *work = nullptr, *mom = nullptr, *lam = nullptr;
@@ -1016,7 +1070,7 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     if (e == cudaSuccess) e = cudaMalloc(&lam, 2 * 27 * n * es);
     const int64_t nblk = (int64_t)((n + 255) / 256);
     const int64_t nslot = nblk * 8;                  // one slot per warp
-    if (e == cudaSuccess) e = cudaMalloc((void **)&acc, (n + 2 * nslot) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&acc, (nd + 2 * nslot) * sizeof(double));
     auto release = [&]() { cudaFree(ck); cudaFree(work); cudaFree(mom); cudaFree(lam); cudaFree(acc); };
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1052,11 +1106,11 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     j.kappa_f = (float)j.kappa;
     j.wss_f = (float)j.wss;
     j.acc = acc;
-    j.blockacc = acc + n;
+    j.blockacc = acc + nd;
     j.nblocks = (int32_t)nblk;
     if (rc == LBM_OK) {
         e = cudaMemsetAsync(lam, 0, 2 * 27 * n * es, c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, (n + 2 * nslot) * sizeof(double), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, (nd + 2 * nslot) * sizeof(double), c->stream);
         if (e != cudaSuccess) rc = cuda_err(c, e, "adjoint buffer clear");
     }
     for (int64_t sgm = nseg - 1; sgm >= 0 && rc == LBM_OK; --sgm) {
@@ -1087,13 +1141,13 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     if (rc == LBM_OK) {
         double *dout = c->partials + lbm::REDUCE_MAX_BLOCKS * 5;
         rc = dispatch(c, [&](auto P) {
-            return lbm::launch_sum_columns<decltype(P)::value>(acc + n, nslot, 2, c->partials,
+            return lbm::launch_sum_columns<decltype(P)::value>(acc + nd, nslot, 2, c->partials,
                                                                lbm::REDUCE_MAX_BLOCKS, dout, c->stream);
         });
         if (rc == LBM_OK) {
             e = cudaMemcpyAsync(host, dout, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
             if (e == cudaSuccess && dJ_dgz)
-                e = cudaMemcpyAsync(dJ_dgz, acc, n * sizeof(double), cudaMemcpyDefault, c->stream);
+                e = cudaMemcpyAsync(dJ_dgz, acc, nd * sizeof(double), cudaMemcpyDefault, c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             if (e != cudaSuccess) rc = cuda_err(c, e, "adjoint results");
         }

@@ -88,10 +88,23 @@ template <> struct Storage<LBM_BF16> {
 };
 
 // ---- per-member description (host fills, device reads) ---------------------------------
+// Storage layouts.  Dense: every cell of the box is stored, index (z ny + y) nx + x.
+// Compact (pipes with half-way or Bouzidi walls): each row (y, z) stores only its run
+// of fluid cells x0(y) .. x0(y) + span(y) - 1, starting on a 64-byte boundary; a plane
+// holds Ps elements and cell (x, y, z) sits at z Ps + rowbase(y) + x - x0(y).  Solid
+// cells have no storage (those walls never touch them), so every DRAM access atom
+// carries fluid data except at the end of a row, and threads map onto stored cells only.
 struct Member {
     int32_t nx, ny, nz, geometry;
-    int64_t off;        // first cell of this member inside each population plane
+    int64_t off;        // first stored cell of this member inside each population plane
     int64_t cells;      // nx * ny * nz
+    int64_t scells;     // stored cells: cells (dense) or nz * Ps (compact)
+    int64_t doff;       // first cell of this member in dense per-cell arrays (statistics)
+    int32_t compact, Ps;
+    uint32_t ps_mul, ps_shr;   // magic division by Ps
+    const int32_t *rowbase;    // compact: [ny] start of row y inside a plane
+    const int32_t *rowx0;      // compact: [ny] first fluid x of row y
+    const uint16_t *rowof;     // compact: [Ps] row of each stored position (0xFFFF: padding)
     int64_t block0;     // first block of this member in a flat launch
     int64_t n_fluid;
     int64_t d2max;      // pipe: fluid iff (2x-nx+1)^2 + (2y-ny+1)^2 <= d2max
@@ -143,7 +156,8 @@ struct StepArgs {
     int32_t nblocks_total;
     int64_t t;                // index of the step being taken
     float f16_scale, f16_inv;
-    double *stats;            // [4][stride] FP64 accumulators (sample steps)
+    double *stats;            // [4][dstride] FP64 accumulators (sample steps), dense cells
+    int64_t dstride;          // cells of all members in dense per-cell arrays
     double st[LBM_MAX_MEMBERS];      // sin(2 pi t / T) per member (0 when off)
     float stf[LBM_MAX_MEMBERS];      // the same in float for the FP32 kernels
     int32_t block0[LBM_MAX_MEMBERS + 1];
@@ -164,7 +178,8 @@ __device__ __forceinline__ int find_member(const StepArgs &a, int blk) {
 // ---- geometry --------------------------------------------------------------------------
 struct CellPos {
     int x, y, z;
-    int32_t lc;              // cell index inside the member
+    int32_t lc;              // storage index inside the member
+    int32_t di;              // dense index (z ny + y) nx + x inside the member
     int32_t ox[3], oy[3], oz[3]; // neighbour offsets for c = -1, 0, +1 (periodic)
     uint32_t nb;             // in-plane fluid mask of the 3x3 neighbourhood
 };
@@ -176,23 +191,74 @@ __host__ __device__ __forceinline__ bool col_fluid(const Member &d, int x, int y
     return X * X + Y * Y <= d.d2max;
 }
 
-__device__ __forceinline__ void cell_setup(const Member &d, uint32_t local, CellPos &p) {
-    const uint32_t q = fastdiv(local, d.nx_mul, d.nx_shr);
-    p.x = (int)(local - q * (uint32_t)d.nx);
+// Neighbour offsets (storage units) for c = -1, 0, +1 along x, y and z.
+__device__ __forceinline__ void cell_offsets(const Member &d, CellPos &p) {
+    if (!d.compact) {
+        const int32_t nx = d.nx, nxy = d.nx * d.ny;
+        p.ox[0] = p.x == 0 ? nx - 1 : -1;
+        p.ox[1] = 0;
+        p.ox[2] = p.x == nx - 1 ? -(nx - 1) : 1;
+        p.oy[0] = p.y == 0 ? (d.ny - 1) * nx : -nx;
+        p.oy[1] = 0;
+        p.oy[2] = p.y == d.ny - 1 ? -(d.ny - 1) * nx : nx;
+        p.oz[0] = p.z == 0 ? (d.nz - 1) * nxy : -nxy;
+        p.oz[1] = 0;
+        p.oz[2] = p.z == d.nz - 1 ? -(d.nz - 1) * nxy : nxy;
+    } else {
+        // rows of a pipe never reach the box edge: no x or y wrap.  A neighbour row
+        // without fluid gets an unused offset (its cells are solid in the mask).
+        const int32_t me = d.rowbase[p.y] - d.rowx0[p.y];
+        p.ox[0] = -1;
+        p.ox[1] = 0;
+        p.ox[2] = 1;
+        p.oy[0] = p.y > 0 ? (d.rowbase[p.y - 1] - d.rowx0[p.y - 1]) - me : 0;
+        p.oy[1] = 0;
+        p.oy[2] = p.y < d.ny - 1 ? (d.rowbase[p.y + 1] - d.rowx0[p.y + 1]) - me : 0;
+        p.oz[0] = p.z == 0 ? (d.nz - 1) * d.Ps : -d.Ps;
+        p.oz[1] = 0;
+        p.oz[2] = p.z == d.nz - 1 ? -(d.nz - 1) * d.Ps : d.Ps;
+    }
+}
+
+// Cell of storage index sidx (< scells) of member d.  Returns whether it is a fluid cell;
+// for a compact padding slot nothing else is set.
+__device__ __forceinline__ bool cell_from_storage(const Member &d, uint32_t sidx, CellPos &p) {
+    if (!d.compact) {
+        const uint32_t q = fastdiv(sidx, d.nx_mul, d.nx_shr);
+        p.x = (int)(sidx - q * (uint32_t)d.nx);
+        p.z = (int)fastdiv(q, d.ny_mul, d.ny_shr);
+        p.y = (int)(q - (uint32_t)p.z * (uint32_t)d.ny);
+        p.lc = (int32_t)sidx;
+        p.di = (int32_t)sidx;
+    } else {
+        p.z = (int)fastdiv(sidx, d.ps_mul, d.ps_shr);
+        const int32_t r = (int32_t)(sidx - (uint32_t)p.z * (uint32_t)d.Ps);
+        const uint16_t y = d.rowof[r];
+        if (y == 0xFFFFu) return false;
+        p.y = y;
+        p.x = d.rowx0[y] + (r - d.rowbase[y]);
+        p.lc = (int32_t)sidx;
+        p.di = (p.z * d.ny + p.y) * d.nx + p.x;
+    }
+    p.nb = d.colmask[p.y * d.nx + p.x];
+    cell_offsets(d, p);
+    return (p.nb >> 4) & 1u;
+}
+
+// Cell of dense index di (< cells).  p.lc is the storage index of a fluid cell (every
+// cell in the dense layout); returns whether the cell is fluid.
+__device__ __forceinline__ bool cell_from_dense(const Member &d, uint32_t di, CellPos &p) {
+    const uint32_t q = fastdiv(di, d.nx_mul, d.nx_shr);
+    p.x = (int)(di - q * (uint32_t)d.nx);
     p.z = (int)fastdiv(q, d.ny_mul, d.ny_shr);
     p.y = (int)(q - (uint32_t)p.z * (uint32_t)d.ny);
-    p.lc = (int32_t)local;
-    const int32_t nx = d.nx, nxy = d.nx * d.ny;
-    p.ox[0] = p.x == 0 ? nx - 1 : -1;
-    p.ox[1] = 0;
-    p.ox[2] = p.x == nx - 1 ? -(nx - 1) : 1;
-    p.oy[0] = p.y == 0 ? (d.ny - 1) * nx : -nx;
-    p.oy[1] = 0;
-    p.oy[2] = p.y == d.ny - 1 ? -(d.ny - 1) * nx : nx;
-    p.oz[0] = p.z == 0 ? (d.nz - 1) * nxy : -nxy;
-    p.oz[1] = 0;
-    p.oz[2] = p.z == d.nz - 1 ? -(d.nz - 1) * nxy : nxy;
-    p.nb = d.colmask[(int32_t)(q - (uint32_t)p.z * (uint32_t)d.ny) * nx + p.x];
+    p.di = (int32_t)di;
+    p.nb = d.colmask[p.y * d.nx + p.x];
+    const bool fluid = (p.nb >> 4) & 1u;
+    if (!d.compact) p.lc = (int32_t)di;
+    else p.lc = fluid ? p.z * d.Ps + d.rowbase[p.y] + (p.x - d.rowx0[p.y]) : -1;
+    cell_offsets(d, p);
+    return fluid;
 }
 
 template <int I>
@@ -351,7 +417,7 @@ __device__ __forceinline__ void acceleration(const Member &d, const CellPos &p, 
     gx = g_of<R>(d, 0);
     gy = g_of<R>(d, 1);
     gz = g_of<R>(d, 2);
-    if (d.gz_field != nullptr) gz += static_cast<const R *>(d.gz_field)[p.lc];
+    if (d.gz_field != nullptr) gz += static_cast<const R *>(d.gz_field)[p.di];
     if (d.trig && t < d.t_end) {
         const R *ft = static_cast<const R *>(d.ftab);
         const R *zt = static_cast<const R *>(d.ztab);

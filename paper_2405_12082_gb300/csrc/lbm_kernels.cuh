@@ -26,10 +26,9 @@ __global__ void __launch_bounds__(BS, MINB) k_step(const __grid_constant__ StepA
     const int m = find_member(a, blockIdx.x);
     const Member &d = a.members[m];
     const uint32_t local = (uint32_t)(blockIdx.x - a.block0[m]) * BS + threadIdx.x;
-    if (local >= (uint32_t)d.cells) return;
+    if (local >= (uint32_t)d.scells) return;
     CellPos p;
-    cell_setup(d, local, p);
-    if (!((p.nb >> 4) & 1u)) return;
+    if (!cell_from_storage(d, local, p)) return;
     const int64_t t = a.times ? a.times[a.tidx].t : a.t;
     const R stv = st_of<R>(a, m);
     R v[Q];
@@ -40,7 +39,7 @@ __global__ void __launch_bounds__(BS, MINB) k_step(const __grid_constant__ StepA
         R sk[5];
         const Macro<R> mm = collide<R>(v, gx, gy, gz, omega_of<R>(d), sk);
         R *mo = static_cast<R *>(a.moments) + p.lc;
-        const int64_t n = d.cells;
+        const int64_t n = d.scells;
         mo[0] = mm.rho;
         mo[n] = mm.ux;
         mo[2 * n] = mm.uy;
@@ -51,12 +50,12 @@ __global__ void __launch_bounds__(BS, MINB) k_step(const __grid_constant__ StepA
         const Macro<R> mm = collide<R>(v, gx, gy, gz, omega_of<R>(d));
         if constexpr (EXTRA == EX_STATS) {
             const double uz = (double)mm.uz;
-            double *s = a.stats + d.off + p.lc;
+            double *s = a.stats + d.doff + p.di;
             const double uz2 = uz * uz;
             s[0] += uz;
-            s[a.stride] += uz2;
-            s[2 * a.stride] += uz2 * uz;
-            s[3 * a.stride] += uz2 * uz2;
+            s[a.dstride] += uz2;
+            s[2 * a.dstride] += uz2 * uz;
+            s[3 * a.dstride] += uz2 * uz2;
         }
     }
     store_pops<P, PAR, WALL>(a, d, p, v);
@@ -120,10 +119,7 @@ __device__ __forceinline__ TileCell tile_cell(const StepArgs &a, int tile) {
         c.m = find_member(a, tile);
         const Member &d = a.members[c.m];
         const uint32_t local = (uint32_t)(tile - a.block0[c.m]) * BS + threadIdx.x;
-        if (local < (uint32_t)d.cells) {
-            cell_setup(d, local, c.p);
-            c.active = (c.p.nb >> 4) & 1u;
-        }
+        if (local < (uint32_t)d.scells) c.active = cell_from_storage(d, local, c.p);
     }
     return c;
 }
@@ -177,12 +173,12 @@ __global__ void __launch_bounds__(BS, MINB) k_step_pipe(const __grid_constant__ 
             const Macro<R> mm = collide<R>(v, gx, gy, gz, omega_of<R>(d));
             if constexpr (EXTRA == EX_STATS) {
                 const double uz = (double)mm.uz;
-                double *sp = a.stats + d.off + cur.p.lc;
+                double *sp = a.stats + d.doff + cur.p.di;
                 const double uz2 = uz * uz;
                 sp[0] += uz;
-                sp[a.stride] += uz2;
-                sp[2 * a.stride] += uz2 * uz;
-                sp[3 * a.stride] += uz2 * uz2;
+                sp[a.dstride] += uz2;
+                sp[2 * a.dstride] += uz2 * uz;
+                sp[3 * a.dstride] += uz2 * uz2;
             }
             store_pops<P, PAR, WALL>(a, d, cur.p, v);
         }
@@ -258,8 +254,7 @@ __global__ void k_moments(const __grid_constant__ StepArgs a, int m, typename St
     const int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (local >= d.cells) return;
     CellPos p;
-    cell_setup(d, (uint32_t)local, p);
-    if (!((p.nb >> 4) & 1u)) {
+    if (!cell_from_dense(d, (uint32_t)local, p)) {
         rho[local] = 0;
         u[local] = 0;
         u[d.cells + local] = 0;
@@ -284,9 +279,9 @@ __global__ void k_get_pops(const __grid_constant__ StepArgs a, int m, double *f)
     const int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (local >= d.cells) return;
     CellPos p;
-    cell_setup(d, (uint32_t)local, p);
+    const bool fluid = cell_from_dense(d, (uint32_t)local, p);
     R v[Q];
-    if (((p.nb >> 4) & 1u) || WALL == LBM_FULLWAY) {
+    if (fluid || WALL == LBM_FULLWAY) {
         load_pops<P, PAR, WALL>(a, d, p, v);
     } else {
 #pragma unroll
@@ -305,8 +300,7 @@ __global__ void k_set_pops(const __grid_constant__ StepArgs a, int m, const doub
     const int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (local >= d.cells) return;
     CellPos p;
-    cell_setup(d, (uint32_t)local, p);
-    if (!((p.nb >> 4) & 1u) && WALL != LBM_FULLWAY) return;
+    if (!cell_from_dense(d, (uint32_t)local, p) && WALL != LBM_FULLWAY) return;
     R v[Q];
     sfor<0, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
@@ -339,12 +333,13 @@ __global__ void k_init(const __grid_constant__ StepArgs a, int m, int profile, d
     const int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (local >= d.cells) return;
     CellPos p;
-    cell_setup(d, (uint32_t)local, p);
     R v[Q];
-    if (!((p.nb >> 4) & 1u)) {
+    if (!cell_from_dense(d, (uint32_t)local, p)) {
+        if (!d.compact) {                               // solid cells are stored only densely
 #pragma unroll
-        for (int i = 0; i < Q; ++i) v[i] = 0;
-        write_state<P, 0, LBM_FULLWAY>(a, d, p, v);   // plain own-slot write at t = 0
+            for (int i = 0; i < Q; ++i) v[i] = 0;
+            write_state<P, 0, LBM_FULLWAY>(a, d, p, v);   // plain own-slot write at t = 0
+        }
         return;
     }
     double ux = 0, uy = 0, uz = 0, drho = 0;
@@ -408,8 +403,7 @@ __global__ void __launch_bounds__(REDUCE_BLOCK) k_reduce(const __grid_constant__
     for (int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; local < d.cells;
          local += (int64_t)gridDim.x * blockDim.x) {
         CellPos p;
-        cell_setup(d, (uint32_t)local, p);
-        if (!((p.nb >> 4) & 1u)) continue;
+        if (!cell_from_dense(d, (uint32_t)local, p)) continue;
         R v[Q];
         load_pops<P, PAR, WALL>(a, d, p, v);
         double dr = 0, jx = 0, jy = 0, jz = 0;
@@ -453,8 +447,7 @@ __device__ double uz_at(const StepArgs &a, const Member &d, int m, int x, int y,
     using R = typename Storage<P>::R;
     if (x < 0 || y < 0 || x >= d.nx || y >= d.ny) return 0.0;
     CellPos p;
-    cell_setup(d, (uint32_t)(((int64_t)z * d.ny + y) * d.nx + x), p);
-    if (!((p.nb >> 4) & 1u)) return 0.0;
+    if (!cell_from_dense(d, (uint32_t)(((int64_t)z * d.ny + y) * d.nx + x), p)) return 0.0;
     R v[Q];
     load_pops<P, PAR, WALL>(a, d, p, v);
     R gx, gy, gz;
@@ -544,7 +537,7 @@ template <int P, int OBJ>
 __device__ __forceinline__ void adjoint_cell(const StepArgs &a, const AdjArgs &j, const Member &d, const CellPos &p,
                                              typename Storage<P>::R &jterm, typename Storage<P>::R &wterm) {
     using R = typename Storage<P>::R;
-    const uint32_t n = (uint32_t)d.cells, lc = (uint32_t)p.lc;
+    const uint32_t n = (uint32_t)d.scells, lc = (uint32_t)p.lc;
     const R *M = static_cast<const R *>(j.moments) + lc;
     const R rho = M[0], ux = M[n], uy = M[2 * n], uz = M[3 * n];
     const R s4 = M[4 * n], s5 = M[5 * n], s6 = M[6 * n], s7 = M[7 * n], s8 = M[8 * n];
@@ -692,7 +685,7 @@ __device__ __forceinline__ void adjoint_cell(const StepArgs &a, const AdjArgs &j
     const R gterm = half * rho * K001 + om1 * half * rho * (q5 * ux + q6 * uy - R(2) * q8 * uz) + half * Auz +
                     (OBJ == LBM_J_UBULK ? half * kap : R(0));
     wterm = -(q4 * s4 + q5 * s5 + q6 * s6 + q7 * s7 + q8 * s8);
-    j.acc[lc] += (double)gterm;
+    j.acc[p.di] += (double)gterm;
 }
 
 // One thread per cell; the objective and dJ/domega terms are summed per block in a fixed
@@ -704,10 +697,9 @@ __global__ void __launch_bounds__(256, LBM_ADJ_MIN_BLOCKS) k_adjoint(const __gri
     const Member &d = a.members[0];
     const int64_t local = (int64_t)blockIdx.x * 256 + threadIdx.x;
     R x0 = 0, x1 = 0;
-    if (local < d.cells) {
+    if (local < d.scells) {
         CellPos p;
-        cell_setup(d, (uint32_t)local, p);
-        if ((p.nb >> 4) & 1u) adjoint_cell<P, OBJ>(a, j, d, p, x0, x1);
+        if (cell_from_storage(d, (uint32_t)local, p)) adjoint_cell<P, OBJ>(a, j, d, p, x0, x1);
     }
     // warp sums of the objective and omega terms in the compute type, added to the
     // warp's own FP64 slots (fixed order, no block barrier)
