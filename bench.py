@@ -220,6 +220,19 @@ def profiled_traffic(precision, workload_name):
     return None
 
 
+def aggregate_ranks(ms, updates, dist=None, device="cpu"):
+    """Whole-job timing across ranks: the slowest rank's time and the sum of every rank's
+    lattice updates (each rank runs its own replica; no exchange on the data path)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms, updates
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def build_single(lbm, cfg, args, stream, rank):
     grid = lbm.make_grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["R"], precision=args.precision, wall="halfway")
     trig = Wk.trigger_dict(h=cfg["h"], R=cfg["R"], nz=cfg["nz"], period=cfg["period"],
@@ -320,11 +333,7 @@ def run_ours(args):
     lbm.lbm_profile_enable(L.ctx, False)
     launches = L.info()["launches"] - launches0
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    updates = n_fluid * LBM_STEPS_PER_STEP * args.steps * world
+    ms, updates = aggregate_ranks(ms, n_fluid * LBM_STEPS_PER_STEP * args.steps, dist, "cuda")
     value = updates / (ms * 1e-3) / 1e6
 
     # end to end through the C ABI with host buffers: upload the state from pinned host

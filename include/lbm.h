@@ -250,6 +250,14 @@ int lbm_set_populations(lbm_ctx *ctx, const double *f);
 int lbm_get_raw(lbm_ctx *ctx, void *buf, size_t bytes);
 int lbm_set_raw(lbm_ctx *ctx, const void *buf, size_t bytes);
 
+/* Checkpoint and resume (the paper keeps snapshots, Sec. II.B; the file format is this
+ * library's own): lbm_save writes the raw populations, t and the statistics
+ * accumulators (if enabled) to `path`; lbm_load restores them into a context created
+ * with the same grids, precision and wall (LBM_EINVAL otherwise), so that stepping on
+ * gives bit-identical results.  Both synchronise the context's stream. */
+int lbm_save(lbm_ctx *ctx, const char *path);
+int lbm_load(lbm_ctx *ctx, const char *path);
+
 /* Sum over fluid cells of the selected member, in FP64: out[0] = sum (rho - 1),
  * out[1..3] = sum of momentum sum_i c_i f_i, out[4] = number of cells with a
  * non-finite population.  out is host memory; the call synchronises. */
@@ -265,6 +273,13 @@ int lbm_stats_enable(lbm_ctx *ctx, int32_t every);
  * and the number of samples taken. */
 int lbm_stats_get(lbm_ctx *ctx, double *acc, int64_t *count);
 
+/* Profiles of the point statistics of Sec. III.B: for every fluid cell of the selected
+ * member the time mean, u_rms = <du^2>^(1/2), S3 = <du^3>/u_rms^3 and S4 = <du^4>/u_rms^4
+ * of u_z (du = u_z - <u_z>_t, from the FP64 sums of lbm_stats_enable), averaged over the
+ * cells whose distance to the axis falls in [b dr, (b+1) dr).  out: host [nbins][6] =
+ * bin centre, cells, mean, u_rms, S3, S4.  1 <= nbins <= 1024.  Synchronises. */
+int lbm_stats_profile(lbm_ctx *ctx, int32_t nbins, double dr, double *out);
+
 /* Coherent-structure analysis of Sec. II.C for the selected member at the
  * current t: for every section s and ring j, u_z is sampled bilinearly at
  * theta_n = 2 pi n / n_theta on the circle of radius r_over_R[j] R and
@@ -273,6 +288,26 @@ int lbm_stats_get(lbm_ctx *ctx, double *acc, int64_t *count);
  * correlation R_uu of Eq. (newcorrelation) at Delta r = 0 (Wiener-Khinchin); the
  * dominant mode is its argmax over 1 <= m <= 10. */
 int lbm_modes(lbm_ctx *ctx, const lbm_modes_cfg *cfg, double *E);
+
+/* ==== analysis of the dominant-mode series (Sec. II.C, Sec. III.C), host functions ==== */
+
+/* Dominant azimuthal mode k* of every section: the m in [m_lo, m_hi] with the largest
+ * E[s][ring][m] (the smallest such m on a tie), E as written by lbm_modes (host memory,
+ * [n_sections][n_rings][n_modes + 1]).  kstar: [n_sections]. */
+int lbm_dominant_modes(const double *E, int32_t n_sections, int32_t n_rings, int32_t n_modes, int32_t ring,
+                       int32_t m_lo, int32_t m_hi, int32_t *kstar);
+
+/* Transition matrix of a mode series (Sec. III.C): over all pairs (k*(t), k*(t + lag))
+ * with both values in [m_lo, m_hi], T[i][j] = P(k*(t + lag) = m_lo + i | k*(t) = m_lo + j),
+ * column-stochastic (a column without visits is zero); lag = d for the series decimated
+ * by d (all d phases pooled).  counts (optional): the raw pair counts, same layout. */
+int lbm_transition_matrix(const int32_t *series, int64_t n, int32_t m_lo, int32_t m_hi, int32_t lag, double *T,
+                          int64_t *counts);
+
+/* Self-mode correlation of Sec. III.C: F[m - m_lo][tau] = <V_m(t) V_m(t + tau)>_t - <V_m>^2,
+ * V_m(t) = 1 if k*(t) = m else 0, for tau = 0..max_lag (< n); the product is averaged
+ * over the n - tau available pairs and <V_m> over the whole series. */
+int lbm_mode_correlation(const int32_t *series, int64_t n, int32_t m_lo, int32_t m_hi, int32_t max_lag, double *F);
 
 /* ==== adjoint ======================================================================== */
 

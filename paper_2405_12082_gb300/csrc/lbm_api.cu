@@ -13,6 +13,9 @@
 using lbm::Member;
 using lbm::StepArgs;
 
+cudaError_t lbm_launch_stats_profile(const double *acc, int64_t stride, const lbm::Member &d, double count, int nbins,
+                                     double dr, double *bins, cudaStream_t s);
+
 struct lbm_ctx {
     int precision = LBM_F32;
     int wall = LBM_HALFWAY;
@@ -1002,6 +1005,30 @@ int lbm_stats_get(lbm_ctx *c, double *acc, int64_t *count) {
     return LBM_OK;
 }
 
+int lbm_stats_profile(lbm_ctx *c, int32_t nbins, double dr, double *out) {
+    if (!c || !out) return LBM_EINVAL;
+    if (!c->stats || c->stats_count < 1) return set_err(c, LBM_EINVAL, "no statistics samples yet");
+    if (nbins < 1 || nbins > 1024 || !(dr > 0)) return set_err(c, LBM_EINVAL, "need 1 <= nbins <= 1024 and dr > 0");
+    const Member &d = c->hm[c->sel];
+    if (d.geometry != LBM_PIPE) return set_err(c, LBM_EINVAL, "radial profiles need a pipe");
+    int rc = ensure_scratch(c, sizeof(double) * 5 * nbins);
+    if (rc) return rc;
+    double *bins = (double *)c->scratch;
+    LBM_CUDA(c, lbm_launch_stats_profile(c->stats + d.doff, c->dense_total, d, (double)c->stats_count, nbins, dr,
+                                         bins, c->stream));
+    c->launches++;
+    std::vector<double> h(5 * (size_t)nbins);
+    LBM_CUDA(c, cudaMemcpyAsync(h.data(), bins, sizeof(double) * 5 * nbins, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < nbins; ++b) {
+        const double n = h[5 * b];
+        out[6 * b + 0] = (b + 0.5) * dr;
+        out[6 * b + 1] = n;
+        for (int k = 1; k < 5; ++k) out[6 * b + 1 + k] = n > 0 ? h[5 * b + k] / n : 0.0;
+    }
+    return LBM_OK;
+}
+
 int lbm_modes(lbm_ctx *c, const lbm_modes_cfg *cfg, double *E) {
     if (!c || !cfg || !E) return LBM_EINVAL;
     const int m = c->sel;
@@ -1194,6 +1221,94 @@ int lbm_fluid_mask(lbm_ctx *c, uint8_t *mask) {
     const Member &d = c->hm[c->sel];
     for (int y = 0; y < d.ny; ++y)
         for (int x = 0; x < d.nx; ++x) mask[(size_t)y * d.nx + x] = col_fluid_host(d, x, y) ? 1 : 0;
+    return LBM_OK;
+}
+
+// ---- checkpoint files ----------------------------------------------------------------
+namespace {
+struct FileHeader {
+    char magic[8];            // "LBMCKPT1"
+    int32_t precision, wall, n_members, stats_every;
+    int64_t stride, dense_total, t, stats_count, pop_bytes, stats_bytes;
+};
+
+bool same_layout(const lbm_ctx *c, const FileHeader &h) {
+    return h.precision == c->precision && h.wall == c->wall && h.n_members == (int32_t)c->hm.size() &&
+           h.stride == c->stride && h.dense_total == c->dense_total;
+}
+}  // namespace
+
+int lbm_save(lbm_ctx *c, const char *path) {
+    if (!c || !path) return LBM_EINVAL;
+    FileHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "LBMCKPT1", 8);
+    h.precision = c->precision;
+    h.wall = c->wall;
+    h.n_members = (int32_t)c->hm.size();
+    h.stats_every = c->stats ? c->stats_every : 0;
+    h.stride = c->stride;
+    h.dense_total = c->dense_total;
+    h.t = c->t;
+    h.stats_count = c->stats_count;
+    h.pop_bytes = (int64_t)27 * c->stride * (int64_t)c->esize;
+    h.stats_bytes = c->stats ? (int64_t)sizeof(double) * 4 * c->dense_total : 0;
+    std::vector<char> host((size_t)std::max<int64_t>(h.pop_bytes, h.stats_bytes));
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) return set_err(c, LBM_EINVAL, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&h, sizeof h, 1, fp) == 1;
+    cudaError_t e = cudaMemcpyAsync(host.data(), c->pops, (size_t)h.pop_bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    ok = ok && e == cudaSuccess && std::fwrite(host.data(), 1, (size_t)h.pop_bytes, fp) == (size_t)h.pop_bytes;
+    if (ok && h.stats_bytes) {
+        e = cudaMemcpyAsync(host.data(), c->stats, (size_t)h.stats_bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        ok = e == cudaSuccess && std::fwrite(host.data(), 1, (size_t)h.stats_bytes, fp) == (size_t)h.stats_bytes;
+    }
+    ok = (std::fclose(fp) == 0) && ok;
+    if (e != cudaSuccess) return cuda_err(c, e, "checkpoint download");
+    if (!ok) return set_err(c, LBM_EINVAL, "writing %s failed", path);
+    return LBM_OK;
+}
+
+int lbm_load(lbm_ctx *c, const char *path) {
+    if (!c || !path) return LBM_EINVAL;
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return set_err(c, LBM_EINVAL, "cannot open %s", path);
+    FileHeader h;
+    bool ok = std::fread(&h, sizeof h, 1, fp) == 1 && std::memcmp(h.magic, "LBMCKPT1", 8) == 0;
+    if (!ok || !same_layout(c, h) || h.pop_bytes != (int64_t)27 * c->stride * (int64_t)c->esize) {
+        std::fclose(fp);
+        return set_err(c, LBM_EINVAL, "%s is not a checkpoint of a context with this layout", path);
+    }
+    std::vector<char> host((size_t)std::max<int64_t>(h.pop_bytes, h.stats_bytes));
+    ok = std::fread(host.data(), 1, (size_t)h.pop_bytes, fp) == (size_t)h.pop_bytes;
+    cudaError_t e = cudaSuccess;
+    if (ok) {
+        e = cudaMemcpyAsync(c->pops, host.data(), (size_t)h.pop_bytes, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    if (ok && e == cudaSuccess && h.stats_bytes) {
+        if (!c->stats) {
+            std::fclose(fp);
+            int rc = lbm_stats_enable(c, h.stats_every);
+            if (rc) return rc;
+            fp = std::fopen(path, "rb");
+            ok = fp && std::fseek(fp, (long)(sizeof h + h.pop_bytes), SEEK_SET) == 0;
+        }
+        ok = ok && std::fread(host.data(), 1, (size_t)h.stats_bytes, fp) == (size_t)h.stats_bytes;
+        if (ok) {
+            e = cudaMemcpyAsync(c->stats, host.data(), (size_t)h.stats_bytes, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        }
+        c->stats_every = h.stats_every;
+        c->stats_count = h.stats_count;
+    }
+    if (fp) std::fclose(fp);
+    if (e != cudaSuccess) return cuda_err(c, e, "checkpoint upload");
+    if (!ok) return set_err(c, LBM_EINVAL, "reading %s failed", path);
+    c->t = h.t;
+    for (size_t m = 0; m < c->hm.size(); ++m) c->mass0_valid[m] = false;
     return LBM_OK;
 }
 

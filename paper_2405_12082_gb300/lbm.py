@@ -104,6 +104,12 @@ def _load():
         "lbm_fluid_mask": [P, P],
         "lbm_reduce_static": [P, I32, I32, I64, P, P],
         "lbm_set_graph": [P, I32],
+        "lbm_save": [P, ctypes.c_char_p],
+        "lbm_stats_profile": [P, I32, D, P],
+        "lbm_dominant_modes": [P, I32, I32, I32, I32, I32, I32, P],
+        "lbm_transition_matrix": [P, I64, I32, I32, I32, P, P],
+        "lbm_mode_correlation": [P, I64, I32, I32, I32, P],
+        "lbm_load": [P, ctypes.c_char_p],
         "lbm_set_variant": [P, I32],
         "lbm_autotune": [P, I32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
     }
@@ -124,7 +130,9 @@ EXPORTED = ("lbm_create", "lbm_ensemble_create", "lbm_free", "lbm_last_error", "
             "lbm_init_fields", "lbm_step", "lbm_set_check", "lbm_moments", "lbm_get_populations",
             "lbm_set_populations", "lbm_get_raw", "lbm_set_raw", "lbm_reduce", "lbm_stats_enable",
             "lbm_stats_get", "lbm_modes", "lbm_adjoint", "lbm_profile_enable", "lbm_profile_read",
-            "lbm_fluid_mask", "lbm_reduce_static", "lbm_set_graph", "lbm_set_variant", "lbm_autotune")
+            "lbm_fluid_mask", "lbm_reduce_static", "lbm_set_graph", "lbm_set_variant", "lbm_autotune",
+            "lbm_save", "lbm_load", "lbm_stats_profile", "lbm_dominant_modes", "lbm_transition_matrix",
+            "lbm_mode_correlation")
 
 
 # ---- marshalling helpers -----------------------------------------------------------------
@@ -318,6 +326,54 @@ def lbm_profile_read(ctx):
     n = ctypes.c_int64()
     _check(ctx, LIB.lbm_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def lbm_stats_profile(ctx, nbins, dr):
+    import numpy as np
+    out = np.empty((nbins, 6))
+    _check(ctx, LIB.lbm_stats_profile(ctx, int(nbins), float(dr), ptr(out)))
+    return out
+
+
+def _host_call(rc, what):
+    if rc != LBM_OK:
+        raise LbmError(rc, what + " rejected its arguments")
+
+
+def lbm_dominant_modes(E, ring=0, m_lo=1, m_hi=10):
+    """E: float64 [n_sections][n_rings][n_modes + 1] (host) -> int32 [n_sections]."""
+    import numpy as np
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    ns, nr, nm1 = E.shape
+    k = np.empty(ns, dtype=np.int32)
+    _host_call(LIB.lbm_dominant_modes(ptr(E), ns, nr, nm1 - 1, ring, m_lo, m_hi, ptr(k)), "lbm_dominant_modes")
+    return k
+
+
+def lbm_transition_matrix(series, m_lo=1, m_hi=10, lag=1):
+    import numpy as np
+    s = np.ascontiguousarray(series, dtype=np.int32)
+    K = m_hi - m_lo + 1
+    T = np.empty((K, K))
+    c = np.empty((K, K), dtype=np.int64)
+    _host_call(LIB.lbm_transition_matrix(ptr(s), s.size, m_lo, m_hi, lag, ptr(T), ptr(c)), "lbm_transition_matrix")
+    return T, c
+
+
+def lbm_mode_correlation(series, m_lo=1, m_hi=10, max_lag=100):
+    import numpy as np
+    s = np.ascontiguousarray(series, dtype=np.int32)
+    F = np.empty((m_hi - m_lo + 1, max_lag + 1))
+    _host_call(LIB.lbm_mode_correlation(ptr(s), s.size, m_lo, m_hi, max_lag, ptr(F)), "lbm_mode_correlation")
+    return F
+
+
+def lbm_save(ctx, path):
+    return _check(ctx, LIB.lbm_save(ctx, os.fsencode(path)))
+
+
+def lbm_load(ctx, path):
+    return _check(ctx, LIB.lbm_load(ctx, os.fsencode(path)))
 
 
 def lbm_set_graph(ctx, chunk):

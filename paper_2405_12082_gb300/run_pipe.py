@@ -1,0 +1,98 @@
+"""Turbulent pipe run following the protocol of Sec. II.B and Sec. III.C on the GPU.
+
+The pipe (R = 48 or R = 96 at Re_tau = 181.3, see workloads.py) starts from the mean
+profile of Sec. II.B plus 5 % noise, is driven by the body force and, for the first
+t_trigger steps, by the four-mode trigger force; after `total` large-eddy turnover times
+(T_LET = R / u*) it has gathered point statistics every 100 steps and the dominant
+azimuthal mode of u_z at 16 cross-sections every `modes_every` steps during the last
+`window` turnover times.  Every number is computed by the library (kernels and its host
+analysis functions); this script only drives the calls and writes an .npz and a JSON
+summary (eigenvalues for the Chapman-Kolmogorov comparison come from numpy).
+
+  python -m paper_2405_12082_gb300.run_pipe --workload c2 --total 30 --window 10 --out run.npz
+"""
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+
+def main(argv=None):
+    from . import lbm
+    from . import workloads as Wk
+    import torch
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f16s", "bf16"])
+    ap.add_argument("--total", type=float, default=30.0, help="run length in T_LET")
+    ap.add_argument("--window", type=float, default=10.0, help="statistics window in T_LET (at the end)")
+    ap.add_argument("--modes-every", type=int, default=20)
+    ap.add_argument("--stats-every", type=int, default=100)
+    ap.add_argument("--check-every", type=int, default=1000)
+    ap.add_argument("--out", default="run.npz")
+    a = ap.parse_args(argv)
+
+    cfg = dict(Wk.C2 if a.workload == "c2" else Wk.C3)
+    R, us, nu = cfg["R"], cfg["u_star"], cfg["nu"]
+    t_let = R / us
+    total = int(round(a.total * t_let))
+    start = total - int(round(a.window * t_let))
+    start -= start % a.stats_every
+    grid = lbm.make_grid(cfg["nx"], cfg["ny"], cfg["nz"], R, precision=a.precision, wall="halfway")
+    trig = Wk.trigger_dict(h=cfg["h"], R=R, nz=cfg["nz"], period=cfg["period"], modes=cfg["trigger_modes"],
+                           t_end=cfg["t_trigger"])
+    L = lbm.Lattice(grid, lbm.lbm_relax(cfg["omega"]), lbm.make_force(g=(0.0, 0.0, cfg["h"]), trigger=trig))
+    L.init("loglaw", noise_amp=cfg["noise"], seed=Wk.SEED)
+    lbm.lbm_set_check(L.ctx, a.check_every, 1e-3)
+    mcfg = lbm.make_modes_cfg(cfg["n_sections"], cfg["r_over_R"], cfg["n_theta"], cfg["n_modes"])
+    n_samples = (total - start) // a.modes_every
+    E = torch.empty((n_samples, cfg["n_sections"], 1, cfg["n_modes"] + 1), dtype=torch.float64, device="cuda")
+    t0 = time.time()
+    L.step(start)
+    lbm.lbm_stats_enable(L.ctx, a.stats_every)
+    ub = []
+    for k in range(n_samples):
+        lbm.lbm_modes(L.ctx, mcfg, E[k])
+        L.step(a.modes_every)
+        if k % max(1, n_samples // 50) == 0:
+            _, u = L.moments()
+            ub.append(float(u[2].sum().item()) / L.info()["n_fluid"])
+    torch.cuda.synchronize()
+    wall = time.time() - t0
+    E_h = E.cpu().numpy()
+    kstar = np.stack([lbm.lbm_dominant_modes(E_h[k], 0, 1, 10) for k in range(n_samples)])   # [time][section]
+    series = kstar[:, 0]
+    T1, counts = lbm.lbm_transition_matrix(series, 1, 10, 1)
+    ck = {}
+    for d in range(1, 6):
+        Td, _ = lbm.lbm_transition_matrix(series, 1, 10, d)
+        ck[d] = {"decimated": sorted(np.abs(np.linalg.eigvals(Td)).tolist(), reverse=True),
+                 "power": sorted(np.abs(np.linalg.eigvals(np.linalg.matrix_power(T1, d))).tolist(), reverse=True)}
+    F = lbm.lbm_mode_correlation(series, 1, 10, min(200, n_samples - 1))
+    prof = lbm.lbm_stats_profile(L.ctx, int(R / 2), 2.0)
+    delta_plus = (R - prof[:, 0]) * us / nu
+    Ub = float(np.mean(ub[len(ub) // 2:])) if ub else float("nan")
+    hist = np.bincount(kstar.ravel(), minlength=11)[1:11]
+    summary = {
+        "workload": cfg["name"], "precision": a.precision, "steps": total, "stats_from": start,
+        "T_LET": t_let, "Re_tau": us * R / nu, "wall_s": wall,
+        "U_b": Ub, "U_b_over_u_star": Ub / us, "Re_bulk": Ub * 2 * R / nu,
+        "mode_pdf": (hist / max(hist.sum(), 1)).tolist(),
+        "transition_diag": np.diag(T1).tolist(),
+        "ck_eigs_d2": ck[2], "profile_u_plus_at_delta_plus": [
+            [float(dp), float(m / us), float(r / us), float(s3), float(s4)]
+            for dp, m, r, s3, s4 in zip(delta_plus, prof[:, 2], prof[:, 3], prof[:, 4], prof[:, 5])
+            if prof[0, 1] >= 0],
+    }
+    np.savez(a.out, kstar=kstar, T1=T1, counts=counts, F=F, profile=prof, delta_plus=delta_plus,
+             ub=np.array(ub), E_last=E_h[-1])
+    L.close()
+    print(json.dumps(summary))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

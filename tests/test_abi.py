@@ -97,3 +97,13 @@ def test_struct_layouts_match_a_c_compiler(lbm_lib, tmp_path):
         assert int(got[st]) == ctypes.sizeof(cls), st
         for f in fields:
             assert int(got["%s.%s" % (st, f)]) == getattr(cls, f).offset, (st, f)
+
+
+def test_create_reports_unsupported_sizes_on_the_host(lbm_lib):
+    """27 x cells beyond 2^32 cannot be indexed by the step kernels: LBM_EUNSUPPORTED before
+    any device allocation."""
+    lbm = lbm_lib
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create(lbm.make_grid(1000, 1000, 200, 0.0, geometry="box"), lbm.lbm_relax(1.2))
+    assert ei.value.status == lbm.LBM_EUNSUPPORTED
+    assert "32-bit" in str(ei.value)

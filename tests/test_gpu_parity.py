@@ -234,3 +234,23 @@ def test_degenerate_sizes(lbm_lib):
     ref.step(4)
     assert rel_err(L.populations(), ref.f, ref.fluid) < 1e-13
     L.close()
+
+
+def test_stats_profile_parity(lbm_lib):
+    """Radial profiles of Sec. III.B statistics (per-cell central moments averaged per bin)."""
+    from oracle import stochastic as St
+    L, ref = make_pair(lbm_lib, 24, 24, 8, 10.0, precision="f64", omega=1.5, g=(0, 0, 1e-4),
+                       trigger=dict(h=1e-4, period=20.0, modes=TRIG_MODES, t_end=1000))
+    f0 = perturbed_state(ref, 808, u_amp=0.02)
+    L.set_populations(f0)
+    lbm_lib.lbm_stats_enable(L.ctx, 2)
+    ref.enable_stats(2)
+    L.step(30)
+    ref.step(30)
+    prof = lbm_lib.lbm_stats_profile(L.ctx, 6, 2.0)
+    expect = St.radial_profile(ref.stats, ref.stats_count, ref.fluid, 24, 24, 6, 2.0)
+    assert np.array_equal(prof[:, :2], expect[:, :2])
+    for k in range(2, 6):
+        scale = np.max(np.abs(expect[:, k]))
+        assert np.max(np.abs(prof[:, k] - expect[:, k])) <= 1e-9 * scale, k
+    L.close()
