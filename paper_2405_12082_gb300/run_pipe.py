@@ -1,6 +1,7 @@
 """Turbulent pipe run following the protocol of Sec. II.B and Sec. III.C on the GPU.
 
-The pipe (R = 48 or R = 96 at Re_tau = 181.3, see workloads.py) starts from the mean
+The pipe (the paper's own 300 x 300 x 600 grid, or the R = 48 / R = 96 pipes at
+Re_tau = 181.3, see workloads.py) starts from the mean
 profile of Sec. II.B plus 5 % noise, is driven by the body force and, for the first
 t_trigger steps, by the four-mode trigger force; after `total` large-eddy turnover times
 (T_LET = R / u*) it has gathered point statistics every 100 steps and the dominant
@@ -14,6 +15,7 @@ summary (eigenvalues for the Chapman-Kolmogorov comparison come from numpy).
 import argparse
 import json
 import math
+import sys
 import time
 
 import numpy as np
@@ -25,9 +27,10 @@ def main(argv=None):
     import torch
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "c2", "c3"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f16s", "bf16"])
     ap.add_argument("--total", type=float, default=30.0, help="run length in T_LET")
+    ap.add_argument("--steps", type=int, default=0, help="run length in steps (overrides --total)")
     ap.add_argument("--window", type=float, default=10.0, help="statistics window in T_LET (at the end)")
     ap.add_argument("--modes-every", type=int, default=20)
     ap.add_argument("--stats-every", type=int, default=100)
@@ -35,11 +38,11 @@ def main(argv=None):
     ap.add_argument("--out", default="run.npz")
     a = ap.parse_args(argv)
 
-    cfg = dict(Wk.C2 if a.workload == "c2" else Wk.C3)
+    cfg = dict({"paper": Wk.C_PAPER, "c2": Wk.C2, "c3": Wk.C3}[a.workload])
     R, us, nu = cfg["R"], cfg["u_star"], cfg["nu"]
     t_let = R / us
-    total = int(round(a.total * t_let))
-    start = total - int(round(a.window * t_let))
+    total = a.steps if a.steps > 0 else int(round(a.total * t_let))
+    start = max(0, total - int(round(a.window * t_let)))
     start -= start % a.stats_every
     grid = lbm.make_grid(cfg["nx"], cfg["ny"], cfg["nz"], R, precision=a.precision, wall="halfway")
     trig = Wk.trigger_dict(h=cfg["h"], R=R, nz=cfg["nz"], period=cfg["period"], modes=cfg["trigger_modes"],
@@ -51,7 +54,14 @@ def main(argv=None):
     n_samples = (total - start) // a.modes_every
     E = torch.empty((n_samples, cfg["n_sections"], 1, cfg["n_modes"] + 1), dtype=torch.float64, device="cuda")
     t0 = time.time()
-    L.step(start)
+    nf = L.info()["n_fluid"]
+    chunk = max(a.modes_every, int(t_let) // 4)
+    while L.info()["t"] < start:                       # progress: U_b / u* four times per T_LET
+        L.step(min(chunk, start - L.info()["t"]))
+        _, u = L.moments()
+        print(json.dumps({"t": L.info()["t"], "U_b/u*": float(u[2].sum().item()) / nf / us,
+                          "max|u_r|": float(torch.sqrt(u[0] ** 2 + u[1] ** 2).max().item())}),
+              file=sys.stderr, flush=True)
     lbm.lbm_stats_enable(L.ctx, a.stats_every)
     ub = []
     for k in range(n_samples):
@@ -64,14 +74,18 @@ def main(argv=None):
     wall = time.time() - t0
     E_h = E.cpu().numpy()
     kstar = np.stack([lbm.lbm_dominant_modes(E_h[k], 0, 1, 10) for k in range(n_samples)])   # [time][section]
-    series = kstar[:, 0]
-    T1, counts = lbm.lbm_transition_matrix(series, 1, 10, 1)
+    # every cross-section gives its own series; counts and correlations are pooled
+    ns = kstar.shape[1]
+    counts = sum(lbm.lbm_transition_matrix(kstar[:, s], 1, 10, 1)[1] for s in range(ns))
+    T1 = counts / np.maximum(counts.sum(axis=0, keepdims=True), 1)
     ck = {}
     for d in range(1, 6):
-        Td, _ = lbm.lbm_transition_matrix(series, 1, 10, d)
+        cd = sum(lbm.lbm_transition_matrix(kstar[:, s], 1, 10, d)[1] for s in range(ns))
+        Td = cd / np.maximum(cd.sum(axis=0, keepdims=True), 1)
         ck[d] = {"decimated": sorted(np.abs(np.linalg.eigvals(Td)).tolist(), reverse=True),
                  "power": sorted(np.abs(np.linalg.eigvals(np.linalg.matrix_power(T1, d))).tolist(), reverse=True)}
-    F = lbm.lbm_mode_correlation(series, 1, 10, min(200, n_samples - 1))
+    max_lag = min(300, n_samples - 1)
+    F = sum(lbm.lbm_mode_correlation(kstar[:, s], 1, 10, max_lag) for s in range(ns)) / ns
     prof = lbm.lbm_stats_profile(L.ctx, int(R / 2), 2.0)
     delta_plus = (R - prof[:, 0]) * us / nu
     Ub = float(np.mean(ub[len(ub) // 2:])) if ub else float("nan")
@@ -82,7 +96,8 @@ def main(argv=None):
         "U_b": Ub, "U_b_over_u_star": Ub / us, "Re_bulk": Ub * 2 * R / nu,
         "mode_pdf": (hist / max(hist.sum(), 1)).tolist(),
         "transition_diag": np.diag(T1).tolist(),
-        "ck_eigs_d2": ck[2], "profile_u_plus_at_delta_plus": [
+        "ck_eigs": ck, "F_mean_over_modes": F.mean(axis=0)[:: max(1, max_lag // 30)].tolist(),
+        "profile_u_plus_at_delta_plus": [
             [float(dp), float(m / us), float(r / us), float(s3), float(s4)]
             for dp, m, r, s3, s4 in zip(delta_plus, prof[:, 2], prof[:, 3], prof[:, 4], prof[:, 5])
             if prof[0, 1] >= 0],

@@ -40,6 +40,16 @@ C3 = dict(C2, name="turbulent pipe 196x196x1152 R=96", nx=196, ny=196, nz=1152, 
           nu=2.0544953116381688e-03, omega=1.9756462640779777, h=3.1363333333333336e-07,
           period=1286.5979381443299, n_theta=512)
 
+# The paper's own run (Sec. II.B): 300 x 300 x 600, R = 149.5, nu = 0.0032 (tau = 0.5096),
+# u* = 0.00388, h = 2 u*^2 / R = 2.01397e-7, T_LET = R / u* = 38530.9; trigger with
+# k_theta = 2, kz = 3, A0 = 50, kappa = 0.5, period 0.052 T_LET = 2003.6, active for the
+# first 3 T_LET = 115,592 steps; rings at r0 = 0.78 R with 1024 samples.
+C_PAPER = dict(name="paper pipe 300x300x600 R=149.5", nx=300, ny=300, nz=600, R=149.5, precision="f32",
+               wall="halfway", nu=0.0032, omega=1.9623233908948192, h=2.0139665551839465e-07,
+               u_star=0.00388, period=2003.6082474226803, t_trigger=115592, noise=0.0028518,
+               stats_every=100, modes_every=20, n_sections=16, r_over_R=(0.78,), n_theta=1024, n_modes=32,
+               trigger_modes=[(2, 1.0, 0.0)])
+
 # Batched ensemble: 16 pipes, R drawn from {16, 20, 24, 32}, length 256, tau = 0.5096.
 C4 = dict(name="ensemble 16 pipes R in {16,20,24,32} L=256", n=16, radii=(16, 20, 24, 32), nz=256,
           nu=0.0032, omega=1.9623233908948192, u_star=0.00388, noise=0.0028518, steps=5000, precision="f32",
