@@ -179,6 +179,25 @@ int lbm_get_info(lbm_ctx *ctx, lbm_info *info);
 int lbm_set_relax(lbm_ctx *ctx, const lbm_relax *relax);
 int lbm_set_force(lbm_ctx *ctx, const lbm_force *force);
 
+/* Collision model of every member, for ablations (default LBM_MRT, LBM_EQ_HERMITE6).
+ * model LBM_MRT: Lambda of Eq. (lambda) in Eq. (m*); LBM_BGK: Lambda = omega I, the
+ * single-relaxation-time operator of Eq. (srt) with the forcing term of Eq. (collision),
+ * f* = f - omega (f - f^eq) + (1 - omega/2) F.  equilibrium LBM_EQ_HERMITE6: Eq.
+ * (BoltzmannEquilibriumDistribution); LBM_EQ_ORDER2: its second-order truncation (the
+ * "LBM-O(2)" of Sec. III.B's comparison), w rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u).
+ * In every case F_i = g . grad_u f_i^eq (with the second-order equilibrium these are
+ * the forcing populations of Guo et al. 2002).  The equilibrium also sets the initial
+ * state written by lbm_init and lbm_init_fields.  Takes effect for the next step; drops
+ * a captured graph.  Models other than (LBM_MRT, LBM_EQ_HERMITE6) run in the default
+ * launch shape only (lbm_set_variant of another shape and lbm_autotune then fail with
+ * LBM_EUNSUPPORTED) and have no adjoint.  Errors: LBM_EINVAL (unknown value),
+ * LBM_EUNSUPPORTED (an ablation model with LBM_F16S or LBM_BF16 storage). */
+#define LBM_MRT 0
+#define LBM_BGK 1
+#define LBM_EQ_HERMITE6 0
+#define LBM_EQ_ORDER2 1
+int lbm_set_collision(lbm_ctx *ctx, int32_t model, int32_t equilibrium);
+
 /* ==== initial state ================================================================== */
 
 /* Every member: f = f^eq(rho = 1, u_0) (Eq. (BoltzmannEquilibriumDistribution)) on

@@ -171,6 +171,44 @@ def macroscopic(f, g):
     return rho, u
 
 
+def feq_order2(rho, u):
+    """Second-order truncation of the Maxwell-Boltzmann equilibrium (the 'LBM-O(2)' of
+    Sec. III.B's comparison): w rho [1 + c.u / cs2 + (c.u)^2 / (2 cs2^2) - u.u / (2 cs2)]."""
+    cu = CX * u[0][None] + CY * u[1][None] + CZ * u[2][None]
+    uu = (u[0] ** 2 + u[1] ** 2 + u[2] ** 2)[None]
+    return W[:, None] * rho[None, :] * (1.0 + cu / CS2 + cu ** 2 / (2 * CS2 ** 2) - uu / (2 * CS2))
+
+
+def guo_order2(rho, u, g):
+    """Guo et al. (2002) forcing populations for the second-order equilibrium:
+    w rho [(c - u) . g / cs2 + (c . u)(c . g) / cs2^2]."""
+    cu = CX * u[0][None] + CY * u[1][None] + CZ * u[2][None]
+    cg = CX * g[0][None] + CY * g[1][None] + CZ * g[2][None]
+    ug = (u[0] * g[0] + u[1] * g[1] + u[2] * g[2])[None]
+    return W[:, None] * rho[None, :] * ((cg - ug) / CS2 + cu * cg / CS2 ** 2)
+
+
+def collide_model(f, g, omega, model="mrt", equilibrium="hermite6"):
+    """Eq. (m*) with a choice of relaxation matrix and equilibrium (ablations).
+
+    model "mrt": Lambda of Eq. (lambda); "bgk": Lambda = omega I, i.e. the single-
+    relaxation-time operator of Eq. (srt) with the forcing term of Eq. (collision).
+    equilibrium "hermite6": Eq. (BoltzmannEquilibriumDistribution) with the printed m^eq
+    and R_k; "order2": the second-order equilibrium with Guo forcing."""
+    rho, u = macroscopic(f, g)
+    m = MT @ f
+    if equilibrium == "hermite6":
+        meq = meq_printed(rho, u)
+        R = forcing_printed(rho, u, g)
+    else:
+        meq = MT @ feq_order2(rho, u)
+        R = MT @ guo_order2(rho, u, g)
+    lam = (relaxation_diag(omega) if model == "mrt" else np.full(27, omega, dtype=np.result_type(omega, 1.0)))
+    lam = lam[:, None]
+    mstar = (1.0 - lam) * m + lam * meq + (1.0 - lam / 2.0) * R
+    return MT_INV @ mstar
+
+
 def collide(f, g, omega):
     """Eq. (collision) in moment space, Eq. (m*), then Eq. (k*f*).
 

@@ -26,7 +26,7 @@ import math
 import numpy as np
 
 from . import rng
-from .collision import collide, feq_hermite, macroscopic
+from .collision import collide, collide_model, feq_hermite, feq_order2, macroscopic
 from .lattice import C, OPP, W
 
 
@@ -143,7 +143,7 @@ class Run:
     """A pipe (or periodic box) simulation, advanced literally step by step."""
 
     def __init__(self, nx, ny, nz, omega, R=None, geometry="pipe", wall="halfway",
-                 g=(0.0, 0.0, 0.0), trigger=None, gz_field=None):
+                 g=(0.0, 0.0, 0.0), trigger=None, gz_field=None, model="mrt", equilibrium="hermite6"):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.R = R if R is not None else 0.0
         self.geometry = geometry
@@ -152,6 +152,7 @@ class Run:
         self.g = np.array(g, dtype=np.float64)
         self.trigger = trigger
         self.gz_field = None if gz_field is None else np.asarray(gz_field, dtype=np.float64)
+        self.model, self.equilibrium = model, equilibrium
         self.fluid = fluid_mask(nx, ny, nz, self.R, geometry)
         self.t = 0
         self.f = np.broadcast_to(W[:, None, None, None], (27, nz, ny, nx)).copy()
@@ -199,7 +200,8 @@ class Run:
         """f = f^eq(rho, u) (Hermite equilibrium) on fluid cells, rest weights elsewhere."""
         self.f = np.broadcast_to(W[:, None, None, None], (27, self.nz, self.ny, self.nx)).copy()
         m = self.fluid
-        self.f[:, m] = feq_hermite(rho[m], u[:, m])
+        feq = feq_hermite if self.equilibrium == "hermite6" else feq_order2
+        self.f[:, m] = feq(rho[m], u[:, m])
         self.t = 0
 
     # -- forces ----------------------------------------------------------------------
@@ -254,7 +256,10 @@ class Run:
             self._accumulate(g)
         m = self.fluid
         fstar = self.f.copy()
-        fstar[:, m] = collide(self.f[:, m], g[:, m], self.omega)
+        if self.model == "mrt" and self.equilibrium == "hermite6":
+            fstar[:, m] = collide(self.f[:, m], g[:, m], self.omega)
+        else:
+            fstar[:, m] = collide_model(self.f[:, m], g[:, m], self.omega, self.model, self.equilibrium)
         if self.wall == "fullway":
             solid = ~m
             fstar[:, solid] = self.f[OPP][:, solid]

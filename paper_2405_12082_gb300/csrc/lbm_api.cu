@@ -51,6 +51,7 @@ struct lbm_ctx {
     int64_t prof_launches_pending = 0;
     int64_t launches = 0;
     int variant = 0;                 // launch shape of the step kernel
+    int collision = 0;               // collision model (lbm::MODEL_* bits)
     // graph-captured chunks of steps
     int32_t graph_chunk = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -65,6 +66,9 @@ struct lbm_ctx {
 namespace {
 
 thread_local std::string g_create_error;
+
+// 128 x 8 threads: the fastest shape in sweeps on GB300 (FP64 has a single shape)
+int default_variant(int precision) { return precision == LBM_F64 ? 0 : 2; }
 
 int set_err(lbm_ctx *c, int code, const char *fmt, ...) {
     char buf[512];
@@ -286,6 +290,7 @@ StepArgs make_args(const lbm_ctx *c, int64_t t) {
     a.f16_inv = c->f16_inv;
     a.stats = c->stats;
     a.dstride = c->dense_total;
+    a.collision = c->collision;
     const int bs = lbm::step_threads(c->precision, c->variant);
     int64_t blk = 0;
     for (size_t m = 0; m < c->hm.size(); ++m) {
@@ -353,7 +358,7 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
     lbm_ctx *c = new lbm_ctx();
     c->precision = prec;
     c->wall = wall;
-    c->variant = prec == LBM_F64 ? 0 : 2;   // 128 x 8: the fastest shape in sweeps on GB300
+    c->variant = default_variant(prec);
     c->stream = (cudaStream_t)stream;
     c->f16_scale = std::ldexp(1.0f, s16);
     c->f16_inv = std::ldexp(1.0f, -s16);
@@ -820,13 +825,32 @@ int lbm_set_variant(lbm_ctx *c, int32_t variant) {
     if (variant < 0 || variant >= lbm::step_variants(c->precision))
         return set_err(c, LBM_EINVAL, "launch-shape variant %d out of range (0..%d)", variant,
                        lbm::step_variants(c->precision) - 1);
+    if (c->collision != 0 && variant != default_variant(c->precision))
+        return set_err(c, LBM_EUNSUPPORTED, "the ablation collision models run in the default launch shape only");
     c->variant = variant;
+    return LBM_OK;
+}
+
+int lbm_set_collision(lbm_ctx *c, int32_t model, int32_t equilibrium) {
+    if (!c) return LBM_EINVAL;
+    if ((model != LBM_MRT && model != LBM_BGK) || (equilibrium != LBM_EQ_HERMITE6 && equilibrium != LBM_EQ_ORDER2))
+        return set_err(c, LBM_EINVAL, "unknown collision model %d / equilibrium %d", model, equilibrium);
+    const int code = (model == LBM_BGK ? lbm::MODEL_BGK : 0) | (equilibrium == LBM_EQ_ORDER2 ? lbm::MODEL_O2 : 0);
+    if (code != 0 && c->precision != LBM_F32 && c->precision != LBM_F64)
+        return set_err(c, LBM_EUNSUPPORTED, "the ablation collision models need F32 or F64 storage");
+    if (code != c->collision) {
+        c->collision = code;
+        c->variant = default_variant(c->precision);
+        drop_graph(c);
+    }
     return LBM_OK;
 }
 
 int lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *variant, double *best_us) {
     if (!c) return LBM_EINVAL;
     if (steps < 2 || steps > 10000) return set_err(c, LBM_EINVAL, "steps must be in 2..10000");
+    if (c->collision != 0)
+        return set_err(c, LBM_EUNSUPPORTED, "the ablation collision models run in the default launch shape only");
     const int nv = lbm::step_variants(c->precision);
     const size_t bytes = (size_t)27 * c->stride * c->esize;
     void *save = nullptr;
@@ -1079,6 +1103,8 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     if (c->hm.size() != 1 || c->wall != LBM_HALFWAY || (c->precision != LBM_F32 && c->precision != LBM_F64) ||
         c->hm[0].geometry != LBM_PIPE)
         return set_err(c, LBM_EUNSUPPORTED, "the adjoint needs a single half-way pipe in F32 or F64 storage");
+    if (c->collision != 0)
+        return set_err(c, LBM_EUNSUPPORTED, "the adjoint is derived for the MRT model with the Hermite equilibrium");
     const Member &d = c->hm[0];
     const int64_t K = checkpoint_every > 0 ? std::min<int64_t>(checkpoint_every, T)
                                            : std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)T)));

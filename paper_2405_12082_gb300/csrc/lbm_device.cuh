@@ -71,10 +71,42 @@ template <> struct Storage<LBM_F64> {
     static __device__ __forceinline__ R ld(const T *p, R) { return *p; }
     static __device__ __forceinline__ void st(T *p, R v, R) { *p = v; }
 };
+// FP32 population accesses.  LBM_LD_HINT / LBM_ST_HINT select the cache policy of the
+// loads and stores (0 = default; loads: 1 = non-coherent path, 2 = L2 256-byte prefetch,
+// 3 = both, 4 = evict-first; stores: 1 = evict-first).  In the AA pattern every slot is
+// read and written by one thread only within a step, so the non-coherent path is safe.
+#ifndef LBM_LD_HINT
+#define LBM_LD_HINT 0
+#endif
+#ifndef LBM_ST_HINT
+#define LBM_ST_HINT 0
+#endif
 template <> struct Storage<LBM_F32> {
     using T = float; using R = float;
-    static __device__ __forceinline__ R ld(const T *p, R) { return *p; }
-    static __device__ __forceinline__ void st(T *p, R v, R) { *p = v; }
+    static __device__ __forceinline__ R ld(const T *p, R) {
+#if LBM_LD_HINT == 1
+        return __ldg(p);
+#elif LBM_LD_HINT == 2
+        float v;
+        asm volatile("ld.global.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        return v;
+#elif LBM_LD_HINT == 3
+        float v;
+        asm volatile("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        return v;
+#elif LBM_LD_HINT == 4
+        return __ldcs(p);
+#else
+        return *p;
+#endif
+    }
+    static __device__ __forceinline__ void st(T *p, R v, R) {
+#if LBM_ST_HINT == 1
+        __stcs(p, v);
+#else
+        *p = v;
+#endif
+    }
 };
 template <> struct Storage<LBM_F16S> {
     using T = __half; using R = float;
@@ -164,6 +196,7 @@ struct StepArgs {
     const StepTime *times;    // when set, t and st come from times[tidx] (graph replays)
     int32_t tidx;
     void *moments;            // adjoint recompute: [9][cells] rho, u, s4..s8 of member 0
+    int32_t collision;        // collision model (MODEL_* bits), the same for every member
 };
 
 __device__ __forceinline__ int find_member(const StepArgs &a, int blk) {
@@ -504,80 +537,139 @@ __device__ __forceinline__ void axis_factors(R u, R g, R (&dl)[3], R (&hd)[3]) {
     hd[2] = hg * (R(6) * u + R(3));
 }
 
+// Collision models: bit 0 selects the relaxation matrix (0: Lambda of Eq. (lambda);
+// 1: Lambda = omega I, the single-relaxation-time operator of Eq. (srt) with the forcing
+// term of Eq. (collision)), bit 1 the equilibrium (0: Eq. (BoltzmannEquilibriumDistribution);
+// 1: its second-order truncation, the "LBM-O(2)" of Sec. III.B, with the forcing
+// populations g . grad_u f^eq, which are Guo et al.'s (2002) for that equilibrium).
+enum { MODEL_MRT_H6 = 0, MODEL_BGK = 1, MODEL_O2 = 2 };
+
+// acc + e x for a lattice component e in {-1, 0, 1}; starting from -0 the sum is exact.
+template <int E, class R> __device__ __forceinline__ R cterm(R acc, R x) {
+    if constexpr (E == 1) return acc + x;
+    else if constexpr (E == -1) return acc - x;
+    else return acc;
+}
+
 // In-place collision of one fluid cell; v holds f - w on entry and f* - w on exit.
 // With s_out, the five non-equilibrium shear moments s_k = m_k - m_k^eq + R_k / 2
 // (k = 4..8) are returned as well (the adjoint stores them).
-template <class R>
+//
+// Every model has the form f* = f^eq + F/2 + (1 - omega) N with F = g . grad_u f^eq:
+// for the MRT, N = sum_{k=4..8} C_k s_k (the other moments relax with rate 1), and s_k
+// is the same for both equilibria since they share their second moments and those of F;
+// for the BGK, N = f - f^eq + F/2.
+template <class R, int MODEL = MODEL_MRT_H6>
 __device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega, R *s_out = nullptr) {
+    constexpr bool bgk = (MODEL & MODEL_BGK) != 0, o2 = (MODEL & MODEL_O2) != 0;
     const Macro<R> mm = macroscopic<R>(v, gx, gy, gz);
     const R rho = mm.rho, ux = mm.ux, uy = mm.uy, uz = mm.uz;
-    // raw second moments m4..m8 (the rest weights contribute nothing to them)
-    R m4 = 0, m5 = 0, m6 = 0, m7 = 0, m8 = 0;
-    sfor<0, Q>([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        constexpr int xy = cx_of(i) * cy_of(i), xz = cx_of(i) * cz_of(i), yz = cy_of(i) * cz_of(i);
-        constexpr int d7 = cx_of(i) * cx_of(i) - cy_of(i) * cy_of(i);
-        constexpr int d8 = cx_of(i) * cx_of(i) - cz_of(i) * cz_of(i);
-        if constexpr (xy == 1) m4 += v[i];
-        if constexpr (xy == -1) m4 -= v[i];
-        if constexpr (xz == 1) m5 += v[i];
-        if constexpr (xz == -1) m5 -= v[i];
-        if constexpr (yz == 1) m6 += v[i];
-        if constexpr (yz == -1) m6 -= v[i];
-        if constexpr (d7 == 1) m7 += v[i];
-        if constexpr (d7 == -1) m7 -= v[i];
-        if constexpr (d8 == 1) m8 += v[i];
-        if constexpr (d8 == -1) m8 -= v[i];
-    });
-    // (1 - omega)(m_k - m_k^eq + R_k / 2), k = 4..8, with the printed m^eq and R
     const R om1 = R(1) - omega;
-    const R s4 = m4 - rho * ux * uy + R(0.5) * rho * (gy * ux + gx * uy);
-    const R s5 = m5 - rho * ux * uz + R(0.5) * rho * (gz * ux + gx * uz);
-    const R s6 = m6 - rho * uy * uz + R(0.5) * rho * (gz * uy + gy * uz);
-    const R s7 = m7 - rho * (ux * ux - uy * uy) + rho * (gx * ux - gy * uy);
-    const R s8 = m8 - rho * (ux * ux - uz * uz) + rho * (gx * ux - gz * uz);
-    if (s_out) {
-        s_out[0] = s4; s_out[1] = s5; s_out[2] = s6; s_out[3] = s7; s_out[4] = s8;
-    }
-    const R a4 = om1 * s4, a5 = om1 * s5, a6 = om1 * s6, a7 = om1 * s7, a8 = om1 * s8;
-    const R s12 = (a7 + a8) * R(1.0 / 6.0);
-    const R s34 = a8 * R(1.0 / 6.0) - a7 * R(1.0 / 3.0);
-    const R s56 = a7 * R(1.0 / 6.0) - a8 * R(1.0 / 3.0);
-    const R q4 = R(0.25) * a4, q5 = R(0.25) * a5, q6 = R(0.25) * a6;
-
-    R dx[3], hx[3], dy[3], hy[3], dz[3], hz[3];
-    axis_factors<R>(ux, gx, dx, hx);
-    axis_factors<R>(uy, gy, dy, hy);
-    axis_factors<R>(uz, gz, dz, hz);
-    // per (cx, cy) pair: Dxy = psi_x psi_y - 1 and the x/y force part
-    R Dxy[3][3], Fxy[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            Dxy[a][b] = dx[a] + dy[b] + dx[a] * dy[b];
-            Fxy[a][b] = hx[a] * (R(1) + dy[b]) + hy[b] * (R(1) + dx[a]);
+    R s12 = 0, s34 = 0, s56 = 0, q4 = 0, q5 = 0, q6 = 0;
+    if constexpr (!bgk) {
+        // raw second moments m4..m8 (the rest weights contribute nothing to them)
+        R m4 = 0, m5 = 0, m6 = 0, m7 = 0, m8 = 0;
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int xy = cx_of(i) * cy_of(i), xz = cx_of(i) * cz_of(i), yz = cy_of(i) * cz_of(i);
+            constexpr int d7 = cx_of(i) * cx_of(i) - cy_of(i) * cy_of(i);
+            constexpr int d8 = cx_of(i) * cx_of(i) - cz_of(i) * cz_of(i);
+            if constexpr (xy == 1) m4 += v[i];
+            if constexpr (xy == -1) m4 -= v[i];
+            if constexpr (xz == 1) m5 += v[i];
+            if constexpr (xz == -1) m5 -= v[i];
+            if constexpr (yz == 1) m6 += v[i];
+            if constexpr (yz == -1) m6 -= v[i];
+            if constexpr (d7 == 1) m7 += v[i];
+            if constexpr (d7 == -1) m7 -= v[i];
+            if constexpr (d8 == 1) m8 += v[i];
+            if constexpr (d8 == -1) m8 -= v[i];
+        });
+        // (1 - omega)(m_k - m_k^eq + R_k / 2), k = 4..8, with the printed m^eq and R
+        const R s4 = m4 - rho * ux * uy + R(0.5) * rho * (gy * ux + gx * uy);
+        const R s5 = m5 - rho * ux * uz + R(0.5) * rho * (gz * ux + gx * uz);
+        const R s6 = m6 - rho * uy * uz + R(0.5) * rho * (gz * uy + gy * uz);
+        const R s7 = m7 - rho * (ux * ux - uy * uy) + rho * (gx * ux - gy * uy);
+        const R s8 = m8 - rho * (ux * ux - uz * uz) + rho * (gx * ux - gz * uz);
+        if (s_out) {
+            s_out[0] = s4; s_out[1] = s5; s_out[2] = s6; s_out[3] = s7; s_out[4] = s8;
         }
+        const R a4 = om1 * s4, a5 = om1 * s5, a6 = om1 * s6, a7 = om1 * s7, a8 = om1 * s8;
+        s12 = (a7 + a8) * R(1.0 / 6.0);
+        s34 = a8 * R(1.0 / 6.0) - a7 * R(1.0 / 3.0);
+        s56 = a7 * R(1.0 / 6.0) - a8 * R(1.0 / 3.0);
+        q4 = R(0.25) * a4;
+        q5 = R(0.25) * a5;
+        q6 = R(0.25) * a6;
+    }
     const R drho = mm.drho;
-    sfor<0, Q>([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        constexpr int a = cx_of(i) + 1, b = cy_of(i) + 1, c = cz_of(i) + 1;
-        const R dxy = Dxy[a][b];
-        const R axy = R(1) + dxy;
-        const R pm1 = dxy + dz[c] * axy;                       // psi_x psi_y psi_z - 1
-        const R frc = Fxy[a][b] * (R(1) + dz[c]) + hz[c] * axy; // (1/2) g . grad psi
-        R f = R(w_of(i)) * (drho + rho * (pm1 + frc));
-        if constexpr (i == 1 || i == 2) f += s12;
-        if constexpr (i == 3 || i == 4) f += s34;
-        if constexpr (i == 5 || i == 6) f += s56;
-        if constexpr (i == 7 || i == 10) f += q4;
-        if constexpr (i == 8 || i == 9) f -= q4;
-        if constexpr (i == 11 || i == 14) f += q5;
-        if constexpr (i == 12 || i == 13) f -= q5;
-        if constexpr (i == 15 || i == 18) f += q6;
-        if constexpr (i == 16 || i == 17) f -= q6;
-        v[i] = f;
-    });
+    if constexpr (!o2) {
+        R dx[3], hx[3], dy[3], hy[3], dz[3], hz[3];
+        axis_factors<R>(ux, gx, dx, hx);
+        axis_factors<R>(uy, gy, dy, hy);
+        axis_factors<R>(uz, gz, dz, hz);
+        // per (cx, cy) pair: Dxy = psi_x psi_y - 1 and the x/y force part
+        R Dxy[3][3], Fxy[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                Dxy[a][b] = dx[a] + dy[b] + dx[a] * dy[b];
+                Fxy[a][b] = hx[a] * (R(1) + dy[b]) + hy[b] * (R(1) + dx[a]);
+            }
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int a = cx_of(i) + 1, b = cy_of(i) + 1, c = cz_of(i) + 1;
+            const R dxy = Dxy[a][b];
+            const R axy = R(1) + dxy;
+            const R pm1 = dxy + dz[c] * axy;                       // psi_x psi_y psi_z - 1
+            const R frc = Fxy[a][b] * (R(1) + dz[c]) + hz[c] * axy; // (1/2) g . grad psi
+            if constexpr (bgk) {
+                const R eq = R(w_of(i)) * (drho + rho * pm1), fh = R(w_of(i)) * rho * frc;
+                v[i] = eq + fh + om1 * (v[i] - eq + fh);
+            } else {
+                R f = R(w_of(i)) * (drho + rho * (pm1 + frc));
+                if constexpr (i == 1 || i == 2) f += s12;
+                if constexpr (i == 3 || i == 4) f += s34;
+                if constexpr (i == 5 || i == 6) f += s56;
+                if constexpr (i == 7 || i == 10) f += q4;
+                if constexpr (i == 8 || i == 9) f -= q4;
+                if constexpr (i == 11 || i == 14) f += q5;
+                if constexpr (i == 12 || i == 13) f -= q5;
+                if constexpr (i == 15 || i == 18) f += q6;
+                if constexpr (i == 16 || i == 17) f -= q6;
+                v[i] = f;
+            }
+        });
+    } else {
+        // second-order equilibrium: f^eq / (w rho) - 1 = 3 c.u + 9/2 (c.u)^2 - 3/2 u.u and
+        // (1/2) g . grad_u of it = 3/2 (c.g - u.g) + 9/2 (c.u)(c.g)
+        const R uu = ux * ux + uy * uy + uz * uz, ug = ux * gx + uy * gy + uz * gz;
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int ex = cx_of(i), ey = cy_of(i), ez = cz_of(i);
+            const R cu = cterm<ez>(cterm<ey>(cterm<ex>(R(-0.0), ux), uy), uz);
+            const R cg = cterm<ez>(cterm<ey>(cterm<ex>(R(-0.0), gx), gy), gz);
+            const R pm1 = R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
+            const R frc = R(1.5) * (cg - ug) + R(4.5) * cu * cg;
+            if constexpr (bgk) {
+                const R eq = R(w_of(i)) * (drho + rho * pm1), fh = R(w_of(i)) * rho * frc;
+                v[i] = eq + fh + om1 * (v[i] - eq + fh);
+            } else {
+                R f = R(w_of(i)) * (drho + rho * (pm1 + frc));
+                if constexpr (i == 1 || i == 2) f += s12;
+                if constexpr (i == 3 || i == 4) f += s34;
+                if constexpr (i == 5 || i == 6) f += s56;
+                if constexpr (i == 7 || i == 10) f += q4;
+                if constexpr (i == 8 || i == 9) f -= q4;
+                if constexpr (i == 11 || i == 14) f += q5;
+                if constexpr (i == 12 || i == 13) f -= q5;
+                if constexpr (i == 15 || i == 18) f += q6;
+                if constexpr (i == 16 || i == 17) f -= q6;
+                v[i] = f;
+            }
+        });
+    }
     return mm;
 }
 

@@ -20,7 +20,7 @@ enum { EX_NONE = 0, EX_STATS = 1, EX_MOMENTS = 2 };
 #define LBM_ADJ_MIN_BLOCKS 3
 #endif
 
-template <int P, int PAR, int WALL, int EXTRA, int BS, int MINB>
+template <int P, int PAR, int WALL, int EXTRA, int BS, int MINB, int MODEL = MODEL_MRT_H6>
 __global__ void __launch_bounds__(BS, MINB) k_step(const __grid_constant__ StepArgs a) {
     using R = typename Storage<P>::R;
     const int m = find_member(a, blockIdx.x);
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(BS, MINB) k_step(const __grid_constant__ StepA
 #pragma unroll
         for (int k = 0; k < 5; ++k) mo[(4 + k) * n] = sk[k];
     } else {
-        const Macro<R> mm = collide<R>(v, gx, gy, gz, omega_of<R>(d));
+        const Macro<R> mm = collide<R, MODEL>(v, gx, gy, gz, omega_of<R>(d));
         if constexpr (EXTRA == EX_STATS) {
             const double uz = (double)mm.uz;
             double *s = a.stats + d.doff + p.di;
@@ -230,6 +230,17 @@ __device__ __forceinline__ void write_state(const StepArgs &a, const Member &d, 
     });
 }
 
+// Shifted second-order equilibrium f^eq(rho, u) - w (no force term).
+template <class R>
+__device__ __forceinline__ void feq_shifted_o2(R drho, R ux, R uy, R uz, R (&v)[Q]) {
+    const R rho = R(1) + drho, uu = ux * ux + uy * uy + uz * uz;
+    sfor<0, Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const R cu = cterm<cz_of(i)>(cterm<cy_of(i)>(cterm<cx_of(i)>(R(-0.0), ux), uy), uz);
+        v[i] = R(w_of(i)) * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
+    });
+}
+
 // Shifted equilibrium f^eq(rho, u) - w in the product form (no force term).
 template <class R>
 __device__ __forceinline__ void feq_shifted(R drho, R ux, R uy, R uz, R (&v)[Q]) {
@@ -367,7 +378,8 @@ __global__ void k_init(const __grid_constant__ StepArgs a, int m, int profile, d
             uz += noise_amp * normal_at(seed, (uint64_t)local, 2);
         }
     }
-    feq_shifted<R>((R)drho, (R)ux, (R)uy, (R)uz, v);
+    if (a.collision & MODEL_O2) feq_shifted_o2<R>((R)drho, (R)ux, (R)uy, (R)uz, v);
+    else feq_shifted<R>((R)drho, (R)ux, (R)uy, (R)uz, v);
     write_state<P, 0, WALL>(a, d, p, v);
 }
 
@@ -781,9 +793,36 @@ cudaError_t launch_step_pipe(int wall, int parity, bool stats, const StepArgs &a
     return cudaGetLastError();
 }
 
+// The ablation models run in one launch shape (the default of the precision).
+template <int P, int BS, int MINB>
+cudaError_t launch_step_model(int wall, int parity, bool stats, const StepArgs &a, cudaStream_t s) {
+    LBM_DISPATCH_WP(wall, parity, {
+        switch (a.collision) {
+            case MODEL_BGK:
+                if (stats) k_step<P, PA, W, EX_STATS, BS, MINB, MODEL_BGK><<<a.nblocks_total, BS, 0, s>>>(a);
+                else k_step<P, PA, W, EX_NONE, BS, MINB, MODEL_BGK><<<a.nblocks_total, BS, 0, s>>>(a);
+                break;
+            case MODEL_O2:
+                if (stats) k_step<P, PA, W, EX_STATS, BS, MINB, MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
+                else k_step<P, PA, W, EX_NONE, BS, MINB, MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
+                break;
+            default:
+                if (stats) k_step<P, PA, W, EX_STATS, BS, MINB, MODEL_BGK | MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
+                else k_step<P, PA, W, EX_NONE, BS, MINB, MODEL_BGK | MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
+                break;
+        }
+    });
+    return cudaGetLastError();
+}
+
 template <int P>
 cudaError_t launch_step(int wall, int parity, bool stats, const StepArgs &a, int variant, cudaStream_t s) {
     if (a.nblocks_total <= 0) return cudaSuccess;
+    if (a.collision != MODEL_MRT_H6) {
+        if constexpr (P == LBM_F64) return launch_step_model<P, 256, 2>(wall, parity, stats, a, s);
+        else if constexpr (P == LBM_F32) return launch_step_model<P, 128, 8>(wall, parity, stats, a, s);
+        else return cudaErrorInvalidValue;
+    }
     if constexpr (P == LBM_F64) {
         return launch_step_shape<P, 256, 2>(wall, parity, stats, a, s);
     } else {

@@ -21,6 +21,8 @@ LBM_PIPE, LBM_BOX = 0, 1
 LBM_HALFWAY, LBM_FULLWAY, LBM_BOUZIDI = 0, 1, 2
 LBM_REST, LBM_LAMINAR, LBM_LOGLAW = 0, 1, 2
 LBM_J_UBULK, LBM_J_WSS = 0, 1
+LBM_MRT, LBM_BGK = 0, 1
+LBM_EQ_HERMITE6, LBM_EQ_ORDER2 = 0, 1
 LBM_MAX_TRIGGER_MODES = 8
 LBM_MAX_MEMBERS = 64
 LBM_STATIC_REDUCE_MAX_BLOCKS = 1216
@@ -29,6 +31,8 @@ LBM_STATIC_REDUCE_MAX_CELLS = 159072862
 PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16": LBM_BF16}
 WALLS = {"halfway": LBM_HALFWAY, "fullway": LBM_FULLWAY, "bouzidi": LBM_BOUZIDI}
 PROFILES = {"rest": LBM_REST, "laminar": LBM_LAMINAR, "loglaw": LBM_LOGLAW}
+MODELS = {"mrt": LBM_MRT, "bgk": LBM_BGK}
+EQUILIBRIA = {"hermite6": LBM_EQ_HERMITE6, "order2": LBM_EQ_ORDER2}
 
 
 class LbmError(RuntimeError):
@@ -85,6 +89,7 @@ def _load():
         "lbm_get_info": [P, ctypes.POINTER(lbm_info)],
         "lbm_set_relax": [P, ctypes.POINTER(lbm_relax)],
         "lbm_set_force": [P, ctypes.POINTER(lbm_force)],
+        "lbm_set_collision": [P, I32, I32],
         "lbm_init": [P, I32, D, U64],
         "lbm_init_fields": [P, P, P],
         "lbm_step": [P, I64],
@@ -132,7 +137,7 @@ EXPORTED = ("lbm_create", "lbm_ensemble_create", "lbm_free", "lbm_last_error", "
             "lbm_stats_get", "lbm_modes", "lbm_adjoint", "lbm_profile_enable", "lbm_profile_read",
             "lbm_fluid_mask", "lbm_reduce_static", "lbm_set_graph", "lbm_set_variant", "lbm_autotune",
             "lbm_save", "lbm_load", "lbm_stats_profile", "lbm_dominant_modes", "lbm_transition_matrix",
-            "lbm_mode_correlation")
+            "lbm_mode_correlation", "lbm_set_collision")
 
 
 # ---- marshalling helpers -----------------------------------------------------------------
@@ -250,6 +255,12 @@ def lbm_set_relax(ctx, relax):
 
 def lbm_set_force(ctx, force):
     return _check(ctx, LIB.lbm_set_force(ctx, ctypes.byref(force)))
+
+
+def lbm_set_collision(ctx, model="mrt", equilibrium="hermite6"):
+    model = MODELS[model] if isinstance(model, str) else model
+    equilibrium = EQUILIBRIA[equilibrium] if isinstance(equilibrium, str) else equilibrium
+    return _check(ctx, LIB.lbm_set_collision(ctx, int(model), int(equilibrium)))
 
 
 def lbm_init(ctx, profile=LBM_REST, noise_amp=0.0, seed=0):

@@ -1,0 +1,133 @@
+"""GPU parity of the ablation collision models against the oracle's literal forms.
+
+The models: the single-relaxation-time operator of Eq. (srt) with the forcing term of
+Eq. (collision) (Lambda = omega I in Eq. (m*)), and the second-order equilibrium of the
+"LBM-O(2)" comparison of Sec. III.B with the forcing g . grad_u f^eq, each alone and
+combined.  The oracle runs them in moment space through the 27 x 27 transforms; the
+kernels use closed forms, so FP64 results agree to rounding (1e-13 relative after a few
+steps, as for the default model).
+"""
+import numpy as np
+import pytest
+
+from _pairs import TRIG_MODES, make_pair, perturbed_state, rel_err
+
+pytestmark = pytest.mark.gpu
+
+MODELS = [("bgk", "hermite6"), ("mrt", "order2"), ("bgk", "order2")]
+
+
+@pytest.mark.parametrize("model,equilibrium", MODELS)
+@pytest.mark.parametrize("wall", ["halfway", "fullway", "bouzidi"])
+def test_step_parity(lbm_lib, model, equilibrium, wall):
+    """Both AA parities, every wall rule, a ragged 23x19x7 pipe, trigger force on."""
+    L, ref = make_pair(lbm_lib, 23, 19, 7, 7.3, precision="f64", wall=wall, omega=1.7, g=(2e-5, -1e-5, 3e-5),
+                       trigger=dict(h=1e-4, period=20.0, modes=TRIG_MODES, t_end=100),
+                       model=model, equilibrium=equilibrium)
+    f0 = perturbed_state(ref, 111)
+    L.set_populations(f0)
+    for n in (1, 2, 3):
+        L.step(n)
+        ref.step(n)
+        assert rel_err(L.populations(), ref.f, ref.fluid) < 1e-13, n
+    L.close()
+
+
+@pytest.mark.parametrize("model,equilibrium", MODELS)
+def test_initial_state_uses_the_model_equilibrium(lbm_lib, model, equilibrium):
+    L, ref = make_pair(lbm_lib, 20, 20, 10, 8.0, precision="f64", omega=1.9, g=(0, 0, 2e-5),
+                       model=model, equilibrium=equilibrium)
+    L.init("loglaw", noise_amp=1e-3, seed=98)
+    ref.init("loglaw", noise_amp=1e-3, seed=98)
+    assert rel_err(L.populations(), ref.f) < 1e-14
+    rho = 1.0 + 0.01 * np.random.default_rng(5).standard_normal((10, 20, 20))
+    u = 0.02 * np.random.default_rng(6).standard_normal((3, 10, 20, 20))
+    lbm_lib.lbm_init_fields(L.ctx, rho, u)
+    ref.init_fields(rho, u)
+    assert rel_err(L.populations(), ref.f, ref.fluid) < 1e-14
+    L.close()
+
+
+@pytest.mark.parametrize("model,equilibrium", MODELS)
+def test_fp32_laminar_velocity_error(lbm_lib, model, equilibrium):
+    """FP32 shifted storage: the same 1e-5 bound on the velocity after 1000 laminar steps
+    as for the default model."""
+    L, ref = make_pair(lbm_lib, 20, 20, 16, 8.0, precision="f32", wall="halfway", omega=1.25, g=(0, 0, 1e-5),
+                       model=model, equilibrium=equilibrium)
+    assert L.info()["variant"] == 2
+    L.init("rest")
+    ref.init("rest")
+    L.step(1000)
+    ref.step(1000)
+    _, u = L.moments()
+    _, uo = ref.moments()
+    m = ref.fluid
+    d = u.double().cpu().numpy()[:, m] - uo[:, m]
+    assert float(np.sqrt(np.sum(d * d) / np.sum(uo[:, m] ** 2))) <= 1e-5
+    L.close()
+
+
+def test_statistics_and_graph_path(lbm_lib):
+    """The statistics variant of the ablation kernel, and graph replays bit-identical to
+    direct launches."""
+    L, ref = make_pair(lbm_lib, 18, 18, 8, 7.0, precision="f64", omega=1.4, g=(0, 0, 1e-4),
+                       model="bgk", equilibrium="order2")
+    f0 = perturbed_state(ref, 414)
+    L.set_populations(f0)
+    lbm_lib.lbm_stats_enable(L.ctx, 3)
+    ref.enable_stats(3)
+    L.step(11)
+    ref.step(11)
+    acc = np.empty((4, 8, 18, 18))
+    assert lbm_lib.lbm_stats_get(L.ctx, acc) == ref.stats_count == 4
+    for k in range(4):
+        assert np.max(np.abs(acc[k] - ref.stats[k])) < 1e-12 * np.max(np.abs(ref.stats[k]))
+    L.close()
+
+    A, _ = make_pair(lbm_lib, 18, 18, 8, 7.0, precision="f32", omega=1.4, g=(0, 0, 1e-4), model="bgk")
+    B, _ = make_pair(lbm_lib, 18, 18, 8, 7.0, precision="f32", omega=1.4, g=(0, 0, 1e-4), model="bgk")
+    for X in (A, B):
+        X.init("laminar", noise_amp=1e-3, seed=3)
+    lbm_lib.lbm_set_graph(B.ctx, 8)
+    A.step(40)
+    B.step(40)
+    assert np.array_equal(A.populations(), B.populations())
+    A.close()
+    B.close()
+
+
+def test_switching_models_and_errors(lbm_lib):
+    lbm = lbm_lib
+    L, ref = make_pair(lbm, 16, 16, 6, 6.0, precision="f32", omega=1.3)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_set_collision(L.ctx, 2, 0)
+    assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_set_collision(L.ctx, 0, 5)
+    assert e.value.status == lbm.LBM_EINVAL
+    lbm.lbm_set_variant(L.ctx, 0)
+    lbm.lbm_set_collision(L.ctx, "bgk", "hermite6")
+    assert L.info()["variant"] == 2                    # back to the default shape
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_set_variant(L.ctx, 1)
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_autotune(L.ctx, 4)
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_adjoint(L.ctx, 4, lbm.LBM_J_UBULK, 0, None)
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
+    # back to the default model: every launch shape again, and the default results
+    lbm.lbm_set_collision(L.ctx, "mrt", "hermite6")
+    lbm.lbm_set_variant(L.ctx, 1)
+    L.init("laminar", noise_amp=1e-3, seed=4)
+    ref.init("laminar", noise_amp=1e-3, seed=4)
+    L.step(6)
+    ref.step(6)
+    assert rel_err(L.populations(), ref.f, ref.fluid) < 1e-6
+    L.close()
+    H, _ = make_pair(lbm, 16, 16, 6, 6.0, precision="f16s", omega=1.3)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_set_collision(H.ctx, "bgk", "hermite6")
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
+    H.close()

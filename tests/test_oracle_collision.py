@@ -133,3 +133,63 @@ def test_relaxation_rate_from_viscosity():
     """omega = (nu / cs2 + 1/2)^{-1}: tau = 0.5096 for the paper's nu = 0.0032."""
     assert abs(1.0 / K.omega_from_nu(0.0032) - 0.5096) < 1e-12
     assert abs(CS2 - 1.0 / 3.0) < 1e-17
+
+
+# ---- ablation models (BGK of Eq. (srt); second-order equilibrium) ----------------------
+
+def test_order2_equilibrium_has_the_maxwellian_moments_to_second_order():
+    rho, u = _rand_state(200, 21)
+    f = K.feq_order2(rho, u)
+    c = C.astype(float)
+    assert np.max(np.abs(f.sum(0) - rho)) < 1e-15
+    assert np.max(np.abs(c.T @ f - rho * u)) < 1e-15
+    for a in range(3):
+        for b in range(3):
+            expect = rho * (u[a] * u[b] + CS2 * (a == b))
+            assert np.max(np.abs((c[:, a] * c[:, b]) @ f - expect)) < 1e-15
+
+
+def test_guo_forcing_moments():
+    """sum F = 0, sum c F = rho g, sum c c F = rho (g u + u g) (Guo et al. 2002)."""
+    rho, u = _rand_state(100, 22)
+    g = 1e-3 * np.random.default_rng(23).standard_normal((3, 100))
+    F = K.guo_order2(rho, u, g)
+    c = C.astype(float)
+    assert np.max(np.abs(F.sum(0))) < 1e-17
+    assert np.max(np.abs(c.T @ F - rho * g)) < 1e-17
+    for a in range(3):
+        for b in range(3):
+            expect = rho * (g[a] * u[b] + u[a] * g[b])
+            assert np.max(np.abs((c[:, a] * c[:, b]) @ F - expect)) < 1e-17
+
+
+@pytest.mark.parametrize("equilibrium", ["hermite6", "order2"])
+def test_bgk_in_moment_space_equals_the_population_form(equilibrium):
+    """Lambda = omega I in Eq. (m*) is Eq. (srt) plus the forcing term of Eq. (collision):
+    f* = f - omega (f - f^eq) + (1 - omega / 2) F."""
+    rho, u0 = _rand_state(150, 24)
+    rng = np.random.default_rng(25)
+    feq_fn = K.feq_hermite if equilibrium == "hermite6" else K.feq_order2
+    f = feq_fn(rho, u0) + 1e-3 * rng.standard_normal((27, 150))
+    g = 1e-4 * rng.standard_normal((3, 150))
+    omega = 1.6
+    fs = K.collide_model(f, g, omega, "bgk", equilibrium)
+    r, u = K.macroscopic(f, g)
+    if equilibrium == "hermite6":
+        h = 1e-30
+        F = np.zeros_like(f)
+        for a in range(3):
+            uc = u.astype(complex)
+            uc[a] += 1j * h
+            F += g[a] * K.feq_hermite(r, uc).imag / h
+    else:
+        F = K.guo_order2(r, u, g)
+    expect = f - omega * (f - feq_fn(r, u)) + (1 - omega / 2) * F
+    assert np.max(np.abs(fs - expect)) < 1e-14      # rounding of the FP64 (M^T)^{-1}
+
+
+def test_mrt_with_hermite6_matches_collide():
+    rho, u0 = _rand_state(100, 26)
+    f = K.feq_hermite(rho, u0) + 1e-3 * np.random.default_rng(27).standard_normal((27, 100))
+    g = 1e-4 * np.ones((3, 100))
+    assert np.max(np.abs(K.collide_model(f, g, 1.3) - K.collide(f, g, 1.3))) < 1e-16

@@ -189,3 +189,23 @@ def test_workload_constants_follow_the_paper_relations():
     assert abs(1.0 / (3 * Wk.C1["nu"] + 0.5) - Wk.C1["omega"]) < 1e-15
     for mem in Wk.ensemble_members():
         assert abs(O.friction_velocity(mem["h"], mem["R"]) - 0.00388) < 1e-15
+
+
+@pytest.mark.parametrize("model,equilibrium", [("bgk", "hermite6"), ("bgk", "order2"), ("mrt", "order2")])
+def test_taylor_green_decay_rate_of_the_ablation_models(model, equilibrium):
+    n, U, omega = 32, 0.01, 1.0
+    k = 2 * math.pi / n
+    X, Y = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    u = np.zeros((3, 1, n, n))
+    u[0, 0] = U * np.sin(k * X) * np.cos(k * Y)
+    u[1, 0] = -U * np.cos(k * X) * np.sin(k * Y)
+    r = O.Run(n, n, 1, omega=omega, geometry="box", model=model, equilibrium=equilibrium)
+    r.init_fields(np.ones((1, n, n)), u)
+    basis = np.sin(k * X) * np.cos(k * Y)
+    amps = []
+    for t in (20, 120):
+        r.step(t - r.t)
+        _, uu = r.moments()
+        amps.append(np.sum(uu[0, 0] * basis) / np.sum(basis * basis))
+    rate = -math.log(amps[1] / amps[0]) / 100
+    assert abs(rate / (2 * O.nu_from_omega(omega) * k * k) - 1) < 0.01
