@@ -335,9 +335,12 @@ int lbm_mode_correlation(const int32_t *series, int64_t n, int32_t m_lo, int32_t
  * gradient with respect to the per-cell axial acceleration, dJ_dgz [nz][ny][nx]
  * (double, host or device), and to the shear rate omega (*dJ_domega).  The
  * reverse sweep recomputes the forward from checkpoints taken every
- * `checkpoint_every` steps (0 = about sqrt(T)).  On return the context holds the
- * state after the T steps.  Needs a context with LBM_HALFWAY wall and LBM_F32 or
- * LBM_F64 precision and no trigger (LBM_EUNSUPPORTED otherwise). */
+ * `checkpoint_every` steps (0 = about sqrt(T)); the steps of the last segment store
+ * their moments during the forward pass and are not recomputed.  On return the
+ * context holds the state after the T steps.  Needs a context with LBM_HALFWAY wall,
+ * LBM_F32 or LBM_F64 precision, no trigger and the default collision model
+ * (LBM_EUNSUPPORTED otherwise).  Allocates its temporaries (checkpoints, moments of
+ * one segment, two adjoint fields) for the duration of the call (LBM_ENOMEM). */
 int lbm_adjoint(lbm_ctx *ctx, int64_t T, int32_t objective, int64_t checkpoint_every,
                 double *J, double *dJ_dgz, double *dJ_domega);
 

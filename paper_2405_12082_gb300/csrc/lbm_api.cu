@@ -1105,6 +1105,7 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
         return set_err(c, LBM_EUNSUPPORTED, "the adjoint needs a single half-way pipe in F32 or F64 storage");
     if (c->collision != 0)
         return set_err(c, LBM_EUNSUPPORTED, "the adjoint is derived for the MRT model with the Hermite equilibrium");
+    if (c->hm[0].trig) return set_err(c, LBM_EUNSUPPORTED, "the adjoint takes no trigger force");
     const Member &d = c->hm[0];
     const int64_t K = checkpoint_every > 0 ? std::min<int64_t>(checkpoint_every, T)
                                            : std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)T)));
@@ -1117,7 +1118,7 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     // segment, two adjoint buffers, FP64 accumulators
     void *ck = nullptr, *work = nullptr, *mom = nullptr, *lam = nullptr;
     double *acc = nullptr;
-    cudaError_t e = cudaMalloc(&ck, pop_bytes * nseg);
+    cudaError_t e = cudaMalloc(&ck, pop_bytes * (size_t)std::max<int64_t>(nseg - 1, 1));
     if (e == cudaSuccess) e = cudaMalloc(&work, pop_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&mom, (size_t)K * 9 * n * es);
     if (e == cudaSuccess) e = cudaMalloc(&lam, 2 * 27 * n * es);
@@ -1131,7 +1132,7 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
         return set_err(c, LBM_ENOMEM, "cannot allocate the adjoint buffers (%lld checkpoints of %zu bytes)",
                        (long long)nseg, pop_bytes);
     }
-    // the forward pass runs with direct launches of the default shape, without statistics
+    // the forward pass runs with direct launches of the context's shape, without statistics
     // or checks; they are restored afterwards
     double *stats_save = c->stats;
     const int64_t check_save = c->check_every;
@@ -1139,15 +1140,29 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     const int32_t chunk_save = c->graph_chunk;
     c->stats = nullptr;
     c->check_every = 0;
-    c->variant = 0;
     c->graph_chunk = 0;
     int rc = LBM_OK;
     const int64_t t0 = c->t;
+    // forward pass: a checkpoint at the start of every segment but the last, whose steps
+    // store their moments at once (its recompute is skipped in the reverse sweep); the
+    // moment-storing kernel has the 256-thread shape (variant 0)
     for (int64_t sgm = 0; sgm < nseg && rc == LBM_OK; ++sgm) {
-        e = cudaMemcpyAsync((char *)ck + sgm * pop_bytes, c->pops, pop_bytes, cudaMemcpyDeviceToDevice, c->stream);
-        if (e != cudaSuccess) { rc = cuda_err(c, e, "checkpoint copy"); break; }
         const int64_t ns = std::min<int64_t>(K, T - sgm * K);
-        for (int64_t k = 0; k < ns && rc == LBM_OK; ++k) rc = step_direct(c);
+        if (sgm < nseg - 1) {
+            e = cudaMemcpyAsync((char *)ck + sgm * pop_bytes, c->pops, pop_bytes, cudaMemcpyDeviceToDevice, c->stream);
+            if (e != cudaSuccess) { rc = cuda_err(c, e, "checkpoint copy"); break; }
+            for (int64_t k = 0; k < ns && rc == LBM_OK; ++k) rc = step_direct(c);
+        } else {
+            c->variant = 0;
+            for (int64_t k = 0; k < ns && rc == LBM_OK; ++k) {
+                StepArgs a = make_args(c, c->t);
+                a.moments = (char *)mom + (size_t)k * 9 * n * es;
+                rc = dispatch(c, [&](auto P) {
+                    return lbm::launch_step_moments<decltype(P)::value>((int)(c->t & 1), a, c->stream);
+                });
+                c->t++;
+            }
+        }
     }
     const int64_t t_end = c->t;
     int64_t nfl = d.n_fluid;
@@ -1168,10 +1183,12 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     }
     for (int64_t sgm = nseg - 1; sgm >= 0 && rc == LBM_OK; --sgm) {
         const int64_t ts = t0 + sgm * K, ns = std::min<int64_t>(K, T - sgm * K);
-        e = cudaMemcpyAsync(work, (char *)ck + sgm * pop_bytes, pop_bytes, cudaMemcpyDeviceToDevice, c->stream);
-        if (e != cudaSuccess) { rc = cuda_err(c, e, "checkpoint restore"); break; }
+        if (sgm < nseg - 1) {
+            e = cudaMemcpyAsync(work, (char *)ck + sgm * pop_bytes, pop_bytes, cudaMemcpyDeviceToDevice, c->stream);
+            if (e != cudaSuccess) { rc = cuda_err(c, e, "checkpoint restore"); break; }
+        }
         // recompute the segment, storing the moments of every step
-        for (int64_t k = 0; k < ns && rc == LBM_OK; ++k) {
+        for (int64_t k = 0; k < ns && rc == LBM_OK && sgm < nseg - 1; ++k) {
             StepArgs a = make_args(c, ts + k);
             a.pops = work;
             a.moments = (char *)mom + (size_t)k * 9 * n * es;

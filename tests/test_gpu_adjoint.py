@@ -27,8 +27,10 @@ def _ctx(lbm, nx, nz, R, omega, g, gz, precision):
     return L
 
 
-@pytest.mark.parametrize("objective", ["ubulk", "wss"])
-def test_fp64_adjoint_matches_the_oracle(lbm_lib, objective):
+@pytest.mark.parametrize("objective,every", [("ubulk", 3), ("wss", 3), ("ubulk", 10), ("wss", 0)])
+def test_fp64_adjoint_matches_the_oracle(lbm_lib, objective, every):
+    """every = 3: four segments, the last of one step; 10: a single segment (all moments
+    stored by the forward pass); 0: ceil(sqrt(10)) = 4, segments of 4, 4, 2."""
     lbm = lbm_lib
     nx, nz, R, omega, T = 14, 6, 5.5, 1.3, 10
     g = (0.0, 0.0, 1e-5)
@@ -41,7 +43,7 @@ def test_fp64_adjoint_matches_the_oracle(lbm_lib, objective):
     L.set_populations(f0)
     dgz = np.zeros((nz, nx, nx))
     obj = lbm.LBM_J_UBULK if objective == "ubulk" else lbm.LBM_J_WSS
-    J, dw = lbm.lbm_adjoint(L.ctx, T, obj, 3, dgz)
+    J, dw = lbm.lbm_adjoint(L.ctx, T, obj, every, dgz)
     Jo, dgzo, dwo = A.adjoint(run, T, objective)
     assert abs(J - Jo) <= 1e-12 * abs(Jo)
     m = run.fluid
@@ -134,3 +136,14 @@ def test_adjoint_leaves_the_forward_state(lbm_lib):
         L.close()
     assert states[0][1] == states[1][1] == 25
     assert np.array_equal(states[0][0], states[1][0])
+
+
+def test_adjoint_rejects_a_trigger(lbm_lib):
+    lbm = lbm_lib
+    grid = lbm.make_grid(16, 16, 8, 6.0, precision="f32", wall="halfway")
+    trig = Wk.trigger_dict(h=1e-5, R=6.0, nz=8, period=50.0, modes=[(2, 1.0, 0.0)], t_end=100)
+    L = lbm.Lattice(grid, lbm.lbm_relax(1.3), lbm.make_force(g=(0, 0, 1e-5), trigger=trig))
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_adjoint(L.ctx, 4, lbm.LBM_J_UBULK, 0, None)
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
+    L.close()
