@@ -89,10 +89,18 @@ typedef struct {
     int32_t f16_log2_scale;
 } lbm_grid;
 
-/* Relaxation matrix of Eq. (lambda): Lambda = diag[1,1,1,1, omega x5, 1 x18], with
- * omega = 1/tau = (nu / c_s^2 + 1/2)^{-1}.  0 < omega < 2. */
+/* Relaxation matrix.  rates == NULL: Lambda of Eq. (lambda), diag[1,1,1,1, omega x5,
+ * 1 x18] (or omega I under lbm_set_collision's LBM_BGK), with omega = 1/tau =
+ * (nu / c_s^2 + 1/2)^{-1}, 0 < omega < 2.  rates != NULL: 27 rates lambda_k in [0, 2], Lambda =
+ * diag(rates) in Eq. (m*), in the moment order of Eq. (Mmatrix) (the library copies them;
+ * the rates of the conserved moments 0..3 have no effect); omega then only sets the
+ * viscosity of the LBM_LAMINAR and LBM_LOGLAW initial profiles.  A context with rates on
+ * any member runs the general collision (both transforms of Eq. (m*) per cell, the
+ * equilibrium chosen by lbm_set_collision), in F32 or F64 storage only, in the default
+ * launch shape, without adjoint. */
 typedef struct {
     double omega;
+    const double *rates;    /* NULL or 27 relaxation rates, moment order of Eq. (Mmatrix) */
 } lbm_relax;
 
 /* Acceleration g(x, t) acting on every fluid cell (Sec. II.B):

@@ -188,13 +188,15 @@ def guo_order2(rho, u, g):
     return W[:, None] * rho[None, :] * ((cg - ug) / CS2 + cu * cg / CS2 ** 2)
 
 
-def collide_model(f, g, omega, model="mrt", equilibrium="hermite6"):
+def collide_model(f, g, omega, model="mrt", equilibrium="hermite6", rates=None):
     """Eq. (m*) with a choice of relaxation matrix and equilibrium (ablations).
 
     model "mrt": Lambda of Eq. (lambda); "bgk": Lambda = omega I, i.e. the single-
     relaxation-time operator of Eq. (srt) with the forcing term of Eq. (collision).
-    equilibrium "hermite6": Eq. (BoltzmannEquilibriumDistribution) with the printed m^eq
-    and R_k; "order2": the second-order equilibrium with Guo forcing."""
+    rates (27 numbers, optional): Lambda = diag(rates) in the moment order of Eq.
+    (Mmatrix), overriding model.  equilibrium "hermite6": Eq.
+    (BoltzmannEquilibriumDistribution) with the printed m^eq and R_k; "order2": the
+    second-order equilibrium with Guo forcing."""
     rho, u = macroscopic(f, g)
     m = MT @ f
     if equilibrium == "hermite6":
@@ -203,7 +205,12 @@ def collide_model(f, g, omega, model="mrt", equilibrium="hermite6"):
     else:
         meq = MT @ feq_order2(rho, u)
         R = MT @ guo_order2(rho, u, g)
-    lam = (relaxation_diag(omega) if model == "mrt" else np.full(27, omega, dtype=np.result_type(omega, 1.0)))
+    if rates is not None:
+        lam = np.asarray(rates, dtype=np.float64)
+    elif model == "mrt":
+        lam = relaxation_diag(omega)
+    else:
+        lam = np.full(27, omega, dtype=np.result_type(omega, 1.0))
     lam = lam[:, None]
     mstar = (1.0 - lam) * m + lam * meq + (1.0 - lam / 2.0) * R
     return MT_INV @ mstar

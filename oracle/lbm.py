@@ -143,7 +143,8 @@ class Run:
     """A pipe (or periodic box) simulation, advanced literally step by step."""
 
     def __init__(self, nx, ny, nz, omega, R=None, geometry="pipe", wall="halfway",
-                 g=(0.0, 0.0, 0.0), trigger=None, gz_field=None, model="mrt", equilibrium="hermite6"):
+                 g=(0.0, 0.0, 0.0), trigger=None, gz_field=None, model="mrt", equilibrium="hermite6",
+                 rates=None):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.R = R if R is not None else 0.0
         self.geometry = geometry
@@ -153,6 +154,7 @@ class Run:
         self.trigger = trigger
         self.gz_field = None if gz_field is None else np.asarray(gz_field, dtype=np.float64)
         self.model, self.equilibrium = model, equilibrium
+        self.rates = None if rates is None else np.asarray(rates, dtype=np.float64)
         self.fluid = fluid_mask(nx, ny, nz, self.R, geometry)
         self.t = 0
         self.f = np.broadcast_to(W[:, None, None, None], (27, nz, ny, nx)).copy()
@@ -256,10 +258,11 @@ class Run:
             self._accumulate(g)
         m = self.fluid
         fstar = self.f.copy()
-        if self.model == "mrt" and self.equilibrium == "hermite6":
+        if self.model == "mrt" and self.equilibrium == "hermite6" and self.rates is None:
             fstar[:, m] = collide(self.f[:, m], g[:, m], self.omega)
         else:
-            fstar[:, m] = collide_model(self.f[:, m], g[:, m], self.omega, self.model, self.equilibrium)
+            fstar[:, m] = collide_model(self.f[:, m], g[:, m], self.omega, self.model, self.equilibrium,
+                                        self.rates)
         if self.wall == "fullway":
             solid = ~m
             fstar[:, solid] = self.f[OPP][:, solid]

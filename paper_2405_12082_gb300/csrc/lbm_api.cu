@@ -1,5 +1,6 @@
 // lbm_api.cu -- the C ABI of include/lbm.h: contexts, validation, memory, launches.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -51,7 +52,10 @@ struct lbm_ctx {
     int64_t prof_launches_pending = 0;
     int64_t launches = 0;
     int variant = 0;                 // launch shape of the step kernel
-    int collision = 0;               // collision model (lbm::MODEL_* bits)
+    int collision = 0;               // collision model of the step kernel (lbm::MODEL_* bits)
+    int model_bits = 0;              // lbm_set_collision: MODEL_BGK, MODEL_O2
+    std::vector<bool> has_rates;     // per member: a general relaxation matrix was given
+    std::vector<std::array<double, 27>> rates;
     // graph-captured chunks of steps
     int32_t graph_chunk = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -211,6 +215,46 @@ void fill_force(Member &d, const lbm_force *f) {
     d.gz_field = f ? f->gz_field : nullptr;
 }
 
+int check_relax(lbm_ctx *c, const lbm_relax *r) {
+    if (!(r->omega > 0.0 && r->omega < 2.0)) return set_err(c, LBM_EINVAL, "omega must be in (0, 2)");
+    if (r->rates)
+        for (int k = 0; k < 27; ++k)
+            if (!(r->rates[k] >= 0.0 && r->rates[k] <= 2.0))
+                return set_err(c, LBM_EINVAL, "relaxation rate %d must lie in [0, 2]", k);
+    return LBM_OK;
+}
+
+// 1 - lambda_k (k = 4..26) of member d: the given rates, else Lambda of Eq. (lambda) or,
+// for the BGK model, omega I.
+void fill_lambda(Member &d, const double *rates, int model_bits) {
+    for (int k = 4; k < 27; ++k) {
+        const double lam = rates ? rates[k] : ((model_bits & lbm::MODEL_BGK) || k <= 8 ? d.omega : 1.0);
+        d.om1k[k - 4] = 1.0 - lam;
+        d.om1kf[k - 4] = (float)(1.0 - lam);
+    }
+}
+
+void drop_graph(lbm_ctx *c);
+
+// Recomputes every member's relaxation table and the step kernel's collision code; a new
+// code returns the launch shape to the default and drops a captured graph.
+int update_collision(lbm_ctx *c) {
+    bool any = false;
+    for (size_t m = 0; m < c->hm.size(); ++m) {
+        fill_lambda(c->hm[m], c->has_rates[m] ? c->rates[m].data() : nullptr, c->model_bits);
+        any = any || c->has_rates[m];
+    }
+    const int code = any ? (lbm::MODEL_RATES | (c->model_bits & lbm::MODEL_O2)) : c->model_bits;
+    if (code != 0 && c->precision != LBM_F32 && c->precision != LBM_F64)
+        return set_err(c, LBM_EUNSUPPORTED, "the ablation collision models need F32 or F64 storage");
+    if (code != c->collision) {
+        c->collision = code;
+        c->variant = default_variant(c->precision);
+        drop_graph(c);
+    }
+    return LBM_OK;
+}
+
 int build_member(lbm_ctx *c, const lbm_grid *g, const lbm_relax *r, const lbm_force *f, Member &d,
                  std::vector<int32_t> *rows = nullptr, std::vector<uint16_t> *rowof = nullptr) {
     if (!g || !r) return set_err(c, LBM_EINVAL, "grid and relax must not be NULL");
@@ -218,8 +262,9 @@ int build_member(lbm_ctx *c, const lbm_grid *g, const lbm_relax *r, const lbm_fo
     const int64_t cells = (int64_t)g->nx * g->ny * g->nz;
     if (cells >= (1ll << 31)) return set_err(c, LBM_EINVAL, "a member may hold at most 2^31-1 cells");
     if (g->geometry != LBM_PIPE && g->geometry != LBM_BOX) return set_err(c, LBM_EINVAL, "unknown geometry");
-    if (!(r->omega > 0.0 && r->omega < 2.0)) return set_err(c, LBM_EINVAL, "omega must be in (0, 2)");
-    int rc = check_force(c, f);
+    int rc = check_relax(c, r);
+    if (rc) return rc;
+    rc = check_force(c, f);
     if (rc) return rc;
     std::memset(&d, 0, sizeof d);
     d.nx = g->nx; d.ny = g->ny; d.nz = g->nz; d.geometry = g->geometry;
@@ -380,6 +425,9 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
         doff += ceil_div(c->hm[k].cells, 64) * 64;
         blk += ceil_div(c->hm[k].scells, 128);       // the smallest launch shape
         c->grids.push_back(grids[k]);
+        c->has_rates.push_back(relax[k].rates != nullptr);
+        c->rates.emplace_back();
+        if (relax[k].rates) std::copy(relax[k].rates, relax[k].rates + 27, c->rates.back().begin());
         lbm_force fz;
         std::memset(&fz, 0, sizeof fz);
         c->forces.push_back(force ? force[k] : fz);
@@ -414,7 +462,13 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
         lbm_free(c);
         return set_err(nullptr, LBM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     }
-    int rc = build_tables(c);
+    int rc = update_collision(c);
+    if (rc) {
+        const std::string msg = c->err;
+        lbm_free(c);
+        return set_err(nullptr, rc, "%s", msg.c_str());
+    }
+    rc = build_tables(c);
     if (rc == LBM_OK) rc = upload_members(c);
     for (size_t m = 0; rc == LBM_OK && m < c->hm.size(); ++m) rc = fill_force_tables(c, (int)m);
     if (rc) {
@@ -566,9 +620,25 @@ int lbm_get_info(lbm_ctx *c, lbm_info *info) {
 
 int lbm_set_relax(lbm_ctx *c, const lbm_relax *r) {
     if (!c || !r) return LBM_EINVAL;
-    if (!(r->omega > 0.0 && r->omega < 2.0)) return set_err(c, LBM_EINVAL, "omega must be in (0, 2)");
-    c->hm[c->sel].omega = r->omega;
-    c->hm[c->sel].omegaf = (float)r->omega;
+    int rc = check_relax(c, r);
+    if (rc) return rc;
+    const int m = c->sel;
+    const bool had = c->has_rates[m];
+    const double omega0 = c->hm[m].omega;
+    const std::array<double, 27> rates0 = c->rates[m];
+    c->hm[m].omega = r->omega;
+    c->hm[m].omegaf = (float)r->omega;
+    c->has_rates[m] = r->rates != nullptr;
+    if (r->rates) std::copy(r->rates, r->rates + 27, c->rates[m].begin());
+    rc = update_collision(c);
+    if (rc) {                               // leave the member as it was
+        c->hm[m].omega = omega0;
+        c->hm[m].omegaf = (float)omega0;
+        c->has_rates[m] = had;
+        c->rates[m] = rates0;
+        update_collision(c);
+        return rc;
+    }
     return upload_members(c);
 }
 
@@ -835,15 +905,15 @@ int lbm_set_collision(lbm_ctx *c, int32_t model, int32_t equilibrium) {
     if (!c) return LBM_EINVAL;
     if ((model != LBM_MRT && model != LBM_BGK) || (equilibrium != LBM_EQ_HERMITE6 && equilibrium != LBM_EQ_ORDER2))
         return set_err(c, LBM_EINVAL, "unknown collision model %d / equilibrium %d", model, equilibrium);
-    const int code = (model == LBM_BGK ? lbm::MODEL_BGK : 0) | (equilibrium == LBM_EQ_ORDER2 ? lbm::MODEL_O2 : 0);
-    if (code != 0 && c->precision != LBM_F32 && c->precision != LBM_F64)
-        return set_err(c, LBM_EUNSUPPORTED, "the ablation collision models need F32 or F64 storage");
-    if (code != c->collision) {
-        c->collision = code;
-        c->variant = default_variant(c->precision);
-        drop_graph(c);
+    const int bits0 = c->model_bits;
+    c->model_bits = (model == LBM_BGK ? lbm::MODEL_BGK : 0) | (equilibrium == LBM_EQ_ORDER2 ? lbm::MODEL_O2 : 0);
+    int rc = update_collision(c);
+    if (rc) {
+        c->model_bits = bits0;
+        update_collision(c);
+        return rc;
     }
-    return LBM_OK;
+    return upload_members(c);
 }
 
 int lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *variant, double *best_us) {

@@ -64,6 +64,81 @@ __device__ __forceinline__ void sfor(F &&f) {
     }
 }
 
+// Row k of the moment basis of Eq. (Mmatrix) at velocity i: m_k = sum_i mt_coef(k, i) f_i.
+__host__ __device__ constexpr int mt_coef(int k, int i) {
+    const int x = cx_of(i), y = cy_of(i), z = cz_of(i);
+    const int x2 = x * x, y2 = y * y, z2 = z * z;
+    switch (k) {
+        case 0: return 1;
+        case 1: return x;
+        case 2: return y;
+        case 3: return z;
+        case 4: return x * y;
+        case 5: return x * z;
+        case 6: return y * z;
+        case 7: return x2 - y2;
+        case 8: return x2 - z2;
+        case 9: return x2 + y2 + z2;
+        case 10: return x * y2 + x * z2;
+        case 11: return x2 * y + y * z2;
+        case 12: return x2 * z + y2 * z;
+        case 13: return x * y2 - x * z2;
+        case 14: return x2 * y - y * z2;
+        case 15: return x2 * z - y2 * z;
+        case 16: return x * y * z;
+        case 17: return x2 * y2 + x2 * z2 + y2 * z2;
+        case 18: return x2 * y2 + x2 * z2 - y2 * z2;
+        case 19: return x2 * y2 - x2 * z2;
+        case 20: return x2 * y * z;
+        case 21: return x * y2 * z;
+        case 22: return x * y * z2;
+        case 23: return x * y2 * z2;
+        case 24: return x2 * y * z2;
+        case 25: return x2 * y2 * z;
+        default: return x2 * y2 * z2;
+    }
+}
+
+// (M^T)^{-1}, the back transform of Eq. (k*f*), by Gauss-Jordan elimination with
+// partial pivoting, evaluated by the compiler: a[i][k] is the weight of moment k in
+// population i.
+struct MtInverse { double a[27][27]; };
+constexpr MtInverse make_mt_inverse() {
+    double A[27][54] = {};
+    for (int k = 0; k < 27; ++k) {
+        for (int i = 0; i < 27; ++i) A[k][i] = (double)mt_coef(k, i);
+        A[k][27 + k] = 1.0;
+    }
+    for (int col = 0; col < 27; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 27; ++r) {
+            const double a = A[r][col] < 0 ? -A[r][col] : A[r][col];
+            const double b = A[piv][col] < 0 ? -A[piv][col] : A[piv][col];
+            if (a > b) piv = r;
+        }
+        for (int j = 0; j < 54; ++j) {
+            const double t = A[col][j];
+            A[col][j] = A[piv][j];
+            A[piv][j] = t;
+        }
+        const double d = A[col][col];
+        for (int j = 0; j < 54; ++j) A[col][j] /= d;
+        for (int r = 0; r < 27; ++r) {
+            if (r == col || A[r][col] == 0.0) continue;
+            const double fct = A[r][col];
+            for (int j = 0; j < 54; ++j) A[r][j] -= fct * A[col][j];
+        }
+    }
+    MtInverse out{};
+    for (int i = 0; i < 27; ++i)
+        for (int k = 0; k < 27; ++k) {
+            const double v = A[i][27 + k];
+            out.a[i][k] = (v < 1e-14 && v > -1e-14) ? 0.0 : v;    // exact zeros of the inverse
+        }
+    return out;
+}
+constexpr MtInverse kMtInv = make_mt_inverse();
+
 // ---- storage ------------------------------------------------------------------------
 template <int P> struct Storage;
 template <> struct Storage<LBM_F64> {
@@ -152,6 +227,10 @@ struct Member {
     const void *gz_field;
     uint32_t nx_mul, nx_shr, ny_mul, ny_shr;   // magic division by nx and ny
     float gf[3], omegaf;       // float copies of g and omega for the FP32 kernels
+    // general relaxation matrix Lambda = diag(lambda_k): 1 - lambda_k for k = 4..26
+    // (k = 0..3 are conserved; read only by the general-rates collision)
+    double om1k[23];
+    float om1kf[23];
     const uint16_t *colmask;   // [ny][nx] in-plane 3x3 fluid mask of every column (device)
     const void *ftab;          // trigger: [3][ny][nx] column factors (P_x, P_y, P_z), compute type
     const void *ztab;          // trigger: [2][nz] cos, sin of kz 2 pi z / L, compute type
@@ -435,6 +514,10 @@ __device__ __forceinline__ void store_pops(const StepArgs &a, const Member &d, c
 template <class R> __device__ __forceinline__ R g_of(const Member &d, int k) {
     if constexpr (sizeof(R) == 4) return d.gf[k]; else return d.g[k];
 }
+template <class R> __device__ __forceinline__ const R *lam1_of(const Member &d) {
+    if constexpr (sizeof(R) == 4) return d.om1kf;
+    else return d.om1k;
+}
 template <class R> __device__ __forceinline__ R omega_of(const Member &d) {
     if constexpr (sizeof(R) == 4) return d.omegaf; else return d.omega;
 }
@@ -542,7 +625,7 @@ __device__ __forceinline__ void axis_factors(R u, R g, R (&dl)[3], R (&hd)[3]) {
 // term of Eq. (collision)), bit 1 the equilibrium (0: Eq. (BoltzmannEquilibriumDistribution);
 // 1: its second-order truncation, the "LBM-O(2)" of Sec. III.B, with the forcing
 // populations g . grad_u f^eq, which are Guo et al.'s (2002) for that equilibrium).
-enum { MODEL_MRT_H6 = 0, MODEL_BGK = 1, MODEL_O2 = 2 };
+enum { MODEL_MRT_H6 = 0, MODEL_BGK = 1, MODEL_O2 = 2, MODEL_RATES = 4 };
 
 // acc + e x for a lattice component e in {-1, 0, 1}; starting from -0 the sum is exact.
 template <int E, class R> __device__ __forceinline__ R cterm(R acc, R x) {
@@ -558,15 +641,22 @@ template <int E, class R> __device__ __forceinline__ R cterm(R acc, R x) {
 // Every model has the form f* = f^eq + F/2 + (1 - omega) N with F = g . grad_u f^eq:
 // for the MRT, N = sum_{k=4..8} C_k s_k (the other moments relax with rate 1), and s_k
 // is the same for both equilibria since they share their second moments and those of F;
-// for the BGK, N = f - f^eq + F/2.
+// for the BGK, N = f - f^eq + F/2.  MODEL_RATES takes a general diagonal Lambda:
+// f* = f^eq + F/2 + (M^T)^{-1} (1 - Lambda) M^T n with n = f - f^eq + F/2, whose moments
+// 0..3 vanish (lam1[k - 4] = 1 - lambda_k).
 template <class R, int MODEL = MODEL_MRT_H6>
-__device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega, R *s_out = nullptr) {
-    constexpr bool bgk = (MODEL & MODEL_BGK) != 0, o2 = (MODEL & MODEL_O2) != 0;
+__device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega, R *s_out = nullptr,
+                                            const R *lam1 = nullptr) {
+    constexpr bool rates = (MODEL & MODEL_RATES) != 0;
+    constexpr bool bgk = !rates && (MODEL & MODEL_BGK) != 0, o2 = (MODEL & MODEL_O2) != 0;
     const Macro<R> mm = macroscopic<R>(v, gx, gy, gz);
     const R rho = mm.rho, ux = mm.ux, uy = mm.uy, uz = mm.uz;
     const R om1 = R(1) - omega;
     R s12 = 0, s34 = 0, s56 = 0, q4 = 0, q5 = 0, q6 = 0;
-    if constexpr (!bgk) {
+    R mk[23];                 // MODEL_RATES: moments 4..26 of n
+#pragma unroll
+    for (int k = 0; k < 23; ++k) mk[k] = 0;
+    if constexpr (!bgk && !rates) {
         // raw second moments m4..m8 (the rest weights contribute nothing to them)
         R m4 = 0, m5 = 0, m6 = 0, m7 = 0, m8 = 0;
         sfor<0, Q>([&](auto ic) {
@@ -603,6 +693,36 @@ __device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega
         q6 = R(0.25) * a6;
     }
     const R drho = mm.drho;
+    // post-collision value of population i from the equilibrium part pm1 = f^eq / (w rho) - 1
+    // and frc = (1/2) g . grad_u (f^eq / (w rho))
+    auto emit = [&](auto ic, R pm1, R frc) {
+        constexpr int i = decltype(ic)::value;
+        if constexpr (rates) {
+            const R eq = R(w_of(i)) * (drho + rho * pm1), fh = R(w_of(i)) * rho * frc;
+            const R ni = v[i] - eq + fh;
+            sfor<4, Q>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                constexpr int cik = mt_coef(k, i);
+                if constexpr (cik != 0) mk[k - 4] += R(cik) * ni;
+            });
+            v[i] = eq + fh;
+        } else if constexpr (bgk) {
+            const R eq = R(w_of(i)) * (drho + rho * pm1), fh = R(w_of(i)) * rho * frc;
+            v[i] = eq + fh + om1 * (v[i] - eq + fh);
+        } else {
+            R f = R(w_of(i)) * (drho + rho * (pm1 + frc));
+            if constexpr (i == 1 || i == 2) f += s12;
+            if constexpr (i == 3 || i == 4) f += s34;
+            if constexpr (i == 5 || i == 6) f += s56;
+            if constexpr (i == 7 || i == 10) f += q4;
+            if constexpr (i == 8 || i == 9) f -= q4;
+            if constexpr (i == 11 || i == 14) f += q5;
+            if constexpr (i == 12 || i == 13) f -= q5;
+            if constexpr (i == 15 || i == 18) f += q6;
+            if constexpr (i == 16 || i == 17) f -= q6;
+            v[i] = f;
+        }
+    };
     if constexpr (!o2) {
         R dx[3], hx[3], dy[3], hy[3], dz[3], hz[3];
         axis_factors<R>(ux, gx, dx, hx);
@@ -624,22 +744,7 @@ __device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega
             const R axy = R(1) + dxy;
             const R pm1 = dxy + dz[c] * axy;                       // psi_x psi_y psi_z - 1
             const R frc = Fxy[a][b] * (R(1) + dz[c]) + hz[c] * axy; // (1/2) g . grad psi
-            if constexpr (bgk) {
-                const R eq = R(w_of(i)) * (drho + rho * pm1), fh = R(w_of(i)) * rho * frc;
-                v[i] = eq + fh + om1 * (v[i] - eq + fh);
-            } else {
-                R f = R(w_of(i)) * (drho + rho * (pm1 + frc));
-                if constexpr (i == 1 || i == 2) f += s12;
-                if constexpr (i == 3 || i == 4) f += s34;
-                if constexpr (i == 5 || i == 6) f += s56;
-                if constexpr (i == 7 || i == 10) f += q4;
-                if constexpr (i == 8 || i == 9) f -= q4;
-                if constexpr (i == 11 || i == 14) f += q5;
-                if constexpr (i == 12 || i == 13) f -= q5;
-                if constexpr (i == 15 || i == 18) f += q6;
-                if constexpr (i == 16 || i == 17) f -= q6;
-                v[i] = f;
-            }
+            emit(ic, pm1, frc);
         });
     } else {
         // second-order equilibrium: f^eq / (w rho) - 1 = 3 c.u + 9/2 (c.u)^2 - 3/2 u.u and
@@ -652,22 +757,21 @@ __device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega
             const R cg = cterm<ez>(cterm<ey>(cterm<ex>(R(-0.0), gx), gy), gz);
             const R pm1 = R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
             const R frc = R(1.5) * (cg - ug) + R(4.5) * cu * cg;
-            if constexpr (bgk) {
-                const R eq = R(w_of(i)) * (drho + rho * pm1), fh = R(w_of(i)) * rho * frc;
-                v[i] = eq + fh + om1 * (v[i] - eq + fh);
-            } else {
-                R f = R(w_of(i)) * (drho + rho * (pm1 + frc));
-                if constexpr (i == 1 || i == 2) f += s12;
-                if constexpr (i == 3 || i == 4) f += s34;
-                if constexpr (i == 5 || i == 6) f += s56;
-                if constexpr (i == 7 || i == 10) f += q4;
-                if constexpr (i == 8 || i == 9) f -= q4;
-                if constexpr (i == 11 || i == 14) f += q5;
-                if constexpr (i == 12 || i == 13) f -= q5;
-                if constexpr (i == 15 || i == 18) f += q6;
-                if constexpr (i == 16 || i == 17) f -= q6;
-                v[i] = f;
-            }
+            emit(ic, pm1, frc);
+        });
+    }
+    if constexpr (rates) {
+#pragma unroll
+        for (int k = 0; k < 23; ++k) mk[k] *= lam1[k];
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            R acc = v[i];
+            sfor<4, Q>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                constexpr double aik = kMtInv.a[i][k];
+                if constexpr (aik != 0.0) acc += R(aik) * mk[k - 4];
+            });
+            v[i] = acc;
         });
     }
     return mm;

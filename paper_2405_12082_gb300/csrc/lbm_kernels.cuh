@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(BS, MINB) k_step(const __grid_constant__ StepA
 #pragma unroll
         for (int k = 0; k < 5; ++k) mo[(4 + k) * n] = sk[k];
     } else {
-        const Macro<R> mm = collide<R, MODEL>(v, gx, gy, gz, omega_of<R>(d));
+        const Macro<R> mm = collide<R, MODEL>(v, gx, gy, gz, omega_of<R>(d), nullptr, lam1_of<R>(d));
         if constexpr (EXTRA == EX_STATS) {
             const double uz = (double)mm.uz;
             double *s = a.stats + d.doff + p.di;
@@ -793,23 +793,34 @@ cudaError_t launch_step_pipe(int wall, int parity, bool stats, const StepArgs &a
     return cudaGetLastError();
 }
 
-// The ablation models run in one launch shape (the default of the precision).
+// The ablation models run in the default thread count of the precision with twice the
+// registers of its shape (half the resident blocks): their populations stay live longer.
 template <int P, int BS, int MINB>
 cudaError_t launch_step_model(int wall, int parity, bool stats, const StepArgs &a, cudaStream_t s) {
+    constexpr int MINB_R = MINB > 1 ? MINB / 2 : 1;
     LBM_DISPATCH_WP(wall, parity, {
         switch (a.collision) {
             case MODEL_BGK:
-                if (stats) k_step<P, PA, W, EX_STATS, BS, MINB, MODEL_BGK><<<a.nblocks_total, BS, 0, s>>>(a);
-                else k_step<P, PA, W, EX_NONE, BS, MINB, MODEL_BGK><<<a.nblocks_total, BS, 0, s>>>(a);
+                if (stats) k_step<P, PA, W, EX_STATS, BS, MINB_R, MODEL_BGK><<<a.nblocks_total, BS, 0, s>>>(a);
+                else k_step<P, PA, W, EX_NONE, BS, MINB_R, MODEL_BGK><<<a.nblocks_total, BS, 0, s>>>(a);
                 break;
             case MODEL_O2:
-                if (stats) k_step<P, PA, W, EX_STATS, BS, MINB, MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
-                else k_step<P, PA, W, EX_NONE, BS, MINB, MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
+                if (stats) k_step<P, PA, W, EX_STATS, BS, MINB_R, MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
+                else k_step<P, PA, W, EX_NONE, BS, MINB_R, MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
                 break;
-            default:
-                if (stats) k_step<P, PA, W, EX_STATS, BS, MINB, MODEL_BGK | MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
-                else k_step<P, PA, W, EX_NONE, BS, MINB, MODEL_BGK | MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
+            case MODEL_BGK | MODEL_O2:
+                if (stats) k_step<P, PA, W, EX_STATS, BS, MINB_R, MODEL_BGK | MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
+                else k_step<P, PA, W, EX_NONE, BS, MINB_R, MODEL_BGK | MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
                 break;
+            case MODEL_RATES:
+                if (stats) k_step<P, PA, W, EX_STATS, BS, MINB_R, MODEL_RATES><<<a.nblocks_total, BS, 0, s>>>(a);
+                else k_step<P, PA, W, EX_NONE, BS, MINB_R, MODEL_RATES><<<a.nblocks_total, BS, 0, s>>>(a);
+                break;
+            case MODEL_RATES | MODEL_O2:
+                if (stats) k_step<P, PA, W, EX_STATS, BS, MINB_R, MODEL_RATES | MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
+                else k_step<P, PA, W, EX_NONE, BS, MINB_R, MODEL_RATES | MODEL_O2><<<a.nblocks_total, BS, 0, s>>>(a);
+                break;
+            default: return cudaErrorInvalidValue;
         }
     });
     return cudaGetLastError();

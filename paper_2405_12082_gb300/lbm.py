@@ -48,7 +48,19 @@ class lbm_grid(ctypes.Structure):
 
 
 class lbm_relax(ctypes.Structure):
-    _fields_ = [("omega", ctypes.c_double)]
+    _fields_ = [("omega", ctypes.c_double), ("rates", ctypes.POINTER(ctypes.c_double))]
+
+
+def make_relax(omega, rates=None):
+    """lbm_relax with an optional 27-entry rate vector (kept alive with the struct)."""
+    r = lbm_relax(float(omega))
+    if rates is not None:
+        if len(rates) != 27:
+            raise ValueError("rates needs 27 entries")
+        arr = (ctypes.c_double * 27)(*[float(x) for x in rates])
+        r.rates = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+        r._rates_keep = arr
+    return r
 
 
 class lbm_force(ctypes.Structure):

@@ -13,9 +13,10 @@ def oracle_trigger(h, R, nz, period, modes, t_end):
 
 
 def make_pair(lbm, nx, ny, nz, R, precision="f64", wall="halfway", omega=1.3, g=(0.0, 0.0, 1e-5),
-              trigger=None, gz=None, geometry="pipe", f16_log2_scale=0, model="mrt", equilibrium="hermite6"):
+              trigger=None, gz=None, geometry="pipe", f16_log2_scale=0, model="mrt", equilibrium="hermite6",
+              rates=None):
     """trigger: None or dict(h, period, modes, t_end); gz: None or a float64 (nz, ny, nx) field;
-    model / equilibrium: the collision model of both sides."""
+    model / equilibrium / rates: the collision model of both sides."""
     grid = lbm.make_grid(nx, ny, nz, R, geometry=geometry, precision=precision, wall=wall,
                          f16_log2_scale=f16_log2_scale)
     tr_dev = tr_or = None
@@ -31,12 +32,12 @@ def make_pair(lbm, nx, ny, nz, R, precision="f64", wall="halfway", omega=1.3, g=
         if precision != "f64":
             gz = gz_dev.double().cpu().numpy()      # the oracle sees exactly the stored values
     force = lbm.make_force(g=g, trigger=tr_dev, gz_field=gz_dev)
-    L = lbm.Lattice(grid, lbm.lbm_relax(omega), force)
+    L = lbm.Lattice(grid, lbm.make_relax(omega, rates), force)
     L._keep.append(gz_dev)
     if (model, equilibrium) != ("mrt", "hermite6"):
         lbm.lbm_set_collision(L.ctx, model, equilibrium)
     ref = O.Run(nx, ny, nz, omega=omega, R=R if geometry == "pipe" else None, geometry=geometry, wall=wall,
-                g=g, trigger=tr_or, gz_field=gz, model=model, equilibrium=equilibrium)
+                g=g, trigger=tr_or, gz_field=gz, model=model, equilibrium=equilibrium, rates=rates)
     return L, ref
 
 

@@ -60,7 +60,7 @@ def test_struct_layouts_match_the_header(lbm_lib):
     """Sizes of the ctypes mirrors equal the C layouts (natural alignment, LP64)."""
     lbm = lbm_lib
     assert ctypes.sizeof(lbm.lbm_grid) == 40
-    assert ctypes.sizeof(lbm.lbm_relax) == 8
+    assert ctypes.sizeof(lbm.lbm_relax) == 16
     assert ctypes.sizeof(lbm.lbm_force) == 264
     assert ctypes.sizeof(lbm.lbm_modes_cfg) == 144
     assert ctypes.sizeof(lbm.lbm_info) == 64
@@ -76,6 +76,7 @@ def test_struct_layouts_match_a_c_compiler(lbm_lib, tmp_path):
     lbm = lbm_lib
     checks = {
         "lbm_grid": ["nx", "R", "precision", "wall", "f16_log2_scale"],
+        "lbm_relax": ["omega", "rates"],
         "lbm_force": ["g", "trigger", "n_modes", "k_theta", "weight", "phase", "A0", "h", "kz", "t_end", "gz_field"],
         "lbm_modes_cfg": ["n_sections", "r_over_R", "n_theta", "n_modes"],
         "lbm_info": ["n_cells", "population_bytes", "n_members", "precision", "launches", "variant", "graph_chunk"],

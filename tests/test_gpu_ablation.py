@@ -131,3 +131,101 @@ def test_switching_models_and_errors(lbm_lib):
         lbm.lbm_set_collision(H.ctx, "bgk", "hermite6")
     assert e.value.status == lbm.LBM_EUNSUPPORTED
     H.close()
+
+
+# ---- a general diagonal relaxation matrix --------------------------------------------------
+
+def _rates(seed, omega):
+    r = np.random.default_rng(seed).uniform(0.8, 1.9, 27)
+    r[:4] = 1.0
+    r[4:9] = omega
+    return r
+
+
+@pytest.mark.parametrize("equilibrium", ["hermite6", "order2"])
+@pytest.mark.parametrize("wall", ["halfway", "bouzidi"])
+def test_general_rates_parity(lbm_lib, equilibrium, wall):
+    rates = _rates(7, 1.7)
+    L, ref = make_pair(lbm_lib, 23, 19, 7, 7.3, precision="f64", wall=wall, omega=1.7, g=(2e-5, -1e-5, 3e-5),
+                       trigger=dict(h=1e-4, period=20.0, modes=TRIG_MODES, t_end=100),
+                       equilibrium=equilibrium, rates=rates)
+    f0 = perturbed_state(ref, 121)
+    L.set_populations(f0)
+    for n in (1, 2, 3):
+        L.step(n)
+        ref.step(n)
+        assert rel_err(L.populations(), ref.f, ref.fluid) < 1e-13, n
+    L.close()
+
+
+def test_paper_rates_through_the_general_transform_match_the_closed_form(lbm_lib):
+    """The 27 x 27 transforms with Lambda of Eq. (lambda) against the closed-form kernel."""
+    lbm = lbm_lib
+    omega = 1.55
+    rates = np.ones(27)
+    rates[4:9] = omega
+    A, ref = make_pair(lbm, 20, 20, 9, 8.2, precision="f64", omega=omega, g=(0, 0, 3e-5))
+    B, _ = make_pair(lbm, 20, 20, 9, 8.2, precision="f64", omega=omega, g=(0, 0, 3e-5), rates=rates)
+    f0 = perturbed_state(ref, 131)
+    A.set_populations(f0)
+    B.set_populations(f0)
+    A.step(7)
+    B.step(7)
+    assert rel_err(B.populations(), A.populations(), ref.fluid) < 1e-13
+    A.close()
+    B.close()
+
+
+def test_rates_in_an_ensemble_and_relax_updates(lbm_lib):
+    """Members with and without rates in one launch, each against the oracle; lbm_set_relax
+    switches a member between the two."""
+    lbm = lbm_lib
+    from oracle import lbm as O
+    rates = _rates(9, 1.4)
+    grids = [lbm.make_grid(18, 18, 6, 7.0, precision="f64", wall="halfway"),
+             lbm.make_grid(14, 14, 6, 5.5, precision="f64", wall="halfway")]
+    relaxes = [lbm.make_relax(1.4, rates), lbm.make_relax(1.2)]
+    forces = [lbm.make_force(g=(0, 0, 2e-5)), lbm.make_force(g=(0, 0, 1e-5))]
+    E = lbm.Lattice(None, None, ensemble=(grids, relaxes, forces))
+    refs = [O.Run(18, 18, 6, omega=1.4, R=7.0, g=(0, 0, 2e-5), rates=rates),
+            O.Run(14, 14, 6, omega=1.2, R=5.5, g=(0, 0, 1e-5))]
+    for k, ref in enumerate(refs):
+        E.select(k)
+        E.set_populations(perturbed_state(ref, 140 + k))
+    E.step(5)
+    for k, ref in enumerate(refs):
+        ref.step(5)
+        E.select(k)
+        assert rel_err(E.populations(), ref.f, ref.fluid) < 1e-13, k
+    # member 0 back to the paper's matrix: the context returns to the closed-form kernel
+    E.select(0)
+    lbm.lbm_set_relax(E.ctx, lbm.make_relax(1.4))
+    refs[0].rates = None
+    E.step(3)
+    for k, ref in enumerate(refs):
+        ref.step(3)
+        E.select(k)
+        assert rel_err(E.populations(), ref.f, ref.fluid) < 1e-13, k
+    E.close()
+
+
+def test_rates_errors(lbm_lib):
+    lbm = lbm_lib
+    grid = lbm.make_grid(12, 12, 4, 4.5, precision="f32")
+    bad = np.ones(27)
+    bad[12] = 2.5
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice(grid, lbm.make_relax(1.2, bad))
+    assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice(lbm.make_grid(12, 12, 4, 4.5, precision="bf16"), lbm.make_relax(1.2, np.ones(27)))
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
+    L = lbm.Lattice(grid, lbm.make_relax(1.2, np.ones(27)))
+    assert L.info()["variant"] == 2
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_adjoint(L.ctx, 4, lbm.LBM_J_UBULK, 0, None)
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_set_relax(L.ctx, lbm.make_relax(1.2, bad))
+    assert e.value.status == lbm.LBM_EINVAL
+    L.close()

@@ -193,3 +193,50 @@ def test_mrt_with_hermite6_matches_collide():
     f = K.feq_hermite(rho, u0) + 1e-3 * np.random.default_rng(27).standard_normal((27, 100))
     g = 1e-4 * np.ones((3, 100))
     assert np.max(np.abs(K.collide_model(f, g, 1.3) - K.collide(f, g, 1.3))) < 1e-16
+
+
+# ---- a general diagonal relaxation matrix ------------------------------------------------
+
+def _noneq(seed, equilibrium="hermite6"):
+    rho, u0 = _rand_state(120, seed)
+    feq_fn = K.feq_hermite if equilibrium == "hermite6" else K.feq_order2
+    rng = np.random.default_rng(seed + 1)
+    return feq_fn(rho, u0) + 1e-3 * rng.standard_normal((27, 120)), 1e-4 * rng.standard_normal((3, 120))
+
+
+def test_rates_reproduce_the_paper_matrix_and_bgk():
+    f, g = _noneq(31)
+    lam = K.relaxation_diag(1.37)
+    assert np.max(np.abs(K.collide_model(f, g, 0.0, rates=lam) - K.collide(f, g, 1.37))) < 1e-16
+    assert np.max(np.abs(K.collide_model(f, g, 0.0, rates=np.full(27, 1.37))
+                         - K.collide_model(f, g, 1.37, "bgk"))) < 1e-16
+
+
+def test_rates_of_the_conserved_moments_do_not_matter():
+    """m_0 = rho and m_1..3 = rho (u - g/2) map to rho and rho (u + g/2) whatever their rate."""
+    f, g = _noneq(32)
+    lam = np.linspace(0.3, 1.8, 27)
+    a = K.collide_model(f, g, 0.0, rates=lam)
+    lam2 = lam.copy()
+    lam2[:4] = [0.1, 1.9, 0.7, 1.3]
+    assert np.max(np.abs(a - K.collide_model(f, g, 0.0, rates=lam2))) < 1e-15
+    rho, u = K.macroscopic(f, g)
+    c = C.astype(float)
+    assert np.max(np.abs(a.sum(0) - rho)) < 1e-14
+    assert np.max(np.abs(c.T @ a - rho * (u + 0.5 * g))) < 1e-14
+
+
+@pytest.mark.parametrize("k", [4, 9, 17, 26])
+def test_a_single_rate_acts_on_its_moment_only(k):
+    """Changing lambda_k changes m*_k by -(delta lambda)(m_k - m_k^eq + R_k / 2) and leaves
+    every other post-collision moment as it was."""
+    f, g = _noneq(40 + k)
+    lam = K.relaxation_diag(1.2)
+    lam2 = lam.copy()
+    lam2[k] = 0.6
+    d = K.MT @ (K.collide_model(f, g, 0.0, rates=lam2) - K.collide_model(f, g, 0.0, rates=lam))
+    rho, u = K.macroscopic(f, g)
+    s = (K.MT @ f)[k] - K.meq_printed(rho, u)[k] + 0.5 * K.forcing_printed(rho, u, g)[k]
+    others = np.delete(np.arange(27), k)
+    assert np.max(np.abs(d[others])) < 1e-14
+    assert np.max(np.abs(d[k] - (-(0.6 - lam[k]) * s))) < 1e-14

@@ -209,3 +209,27 @@ def test_taylor_green_decay_rate_of_the_ablation_models(model, equilibrium):
         amps.append(np.sum(uu[0, 0] * basis) / np.sum(basis * basis))
     rate = -math.log(amps[1] / amps[0]) / 100
     assert abs(rate / (2 * O.nu_from_omega(omega) * k * k) - 1) < 0.01
+
+
+def test_taylor_green_decay_is_set_by_the_shear_rates_alone():
+    """With the non-conserved, non-shear moments relaxed at 1.5 instead of 1 (a general
+    Lambda), the shear wave still decays at 2 nu k^2 with nu from the shear rate."""
+    n, U, omega = 32, 0.01, 1.0
+    k = 2 * math.pi / n
+    X, Y = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    u = np.zeros((3, 1, n, n))
+    u[0, 0] = U * np.sin(k * X) * np.cos(k * Y)
+    u[1, 0] = -U * np.cos(k * X) * np.sin(k * Y)
+    rates = np.full(27, 1.5)
+    rates[:4] = 1.0
+    rates[4:9] = omega
+    r = O.Run(n, n, 1, omega=omega, geometry="box", rates=rates)
+    r.init_fields(np.ones((1, n, n)), u)
+    basis = np.sin(k * X) * np.cos(k * Y)
+    amps = []
+    for t in (20, 120):
+        r.step(t - r.t)
+        _, uu = r.moments()
+        amps.append(np.sum(uu[0, 0] * basis) / np.sum(basis * basis))
+    rate = -math.log(amps[1] / amps[0]) / 100
+    assert abs(rate / (2 * O.nu_from_omega(omega) * k * k) - 1) < 0.01
