@@ -146,42 +146,10 @@ template <> struct Storage<LBM_F64> {
     static __device__ __forceinline__ R ld(const T *p, R) { return *p; }
     static __device__ __forceinline__ void st(T *p, R v, R) { *p = v; }
 };
-// FP32 population accesses.  LBM_LD_HINT / LBM_ST_HINT select the cache policy of the
-// loads and stores (0 = default; loads: 1 = non-coherent path, 2 = L2 256-byte prefetch,
-// 3 = both, 4 = evict-first; stores: 1 = evict-first).  In the AA pattern every slot is
-// read and written by one thread only within a step, so the non-coherent path is safe.
-#ifndef LBM_LD_HINT
-#define LBM_LD_HINT 0
-#endif
-#ifndef LBM_ST_HINT
-#define LBM_ST_HINT 0
-#endif
 template <> struct Storage<LBM_F32> {
     using T = float; using R = float;
-    static __device__ __forceinline__ R ld(const T *p, R) {
-#if LBM_LD_HINT == 1
-        return __ldg(p);
-#elif LBM_LD_HINT == 2
-        float v;
-        asm volatile("ld.global.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
-        return v;
-#elif LBM_LD_HINT == 3
-        float v;
-        asm volatile("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
-        return v;
-#elif LBM_LD_HINT == 4
-        return __ldcs(p);
-#else
-        return *p;
-#endif
-    }
-    static __device__ __forceinline__ void st(T *p, R v, R) {
-#if LBM_ST_HINT == 1
-        __stcs(p, v);
-#else
-        *p = v;
-#endif
-    }
+    static __device__ __forceinline__ R ld(const T *p, R) { return *p; }
+    static __device__ __forceinline__ void st(T *p, R v, R) { *p = v; }
 };
 template <> struct Storage<LBM_F16S> {
     using T = __half; using R = float;
