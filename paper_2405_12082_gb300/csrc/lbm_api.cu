@@ -123,7 +123,9 @@ int build_tables(lbm_ctx *c) {
         const Member &d = c->hm[m];
         const size_t ncol = (size_t)d.nx * d.ny;
         at_rows[m] = total;
-        if (d.compact) total += align256(c->rows[m].size() * 4) + align256(c->rowof[m].size() * 2);
+        if (d.compact)
+            total += align256(c->rows[m].size() * 4) + align256(c->rowof[m].size() * 2) +
+                     align256(c->rowof[m].size() * sizeof(int4));
         at[3 * m] = total; total += align256(ncol * 2);
         at[3 * m + 1] = total; total += align256(3 * ncol * es);
         at[3 * m + 2] = total; total += align256(2 * (size_t)d.nz * es);
@@ -157,6 +159,22 @@ int build_tables(lbm_ctx *c) {
             d.rowbase = (const int32_t *)(g + at_rows[m]);
             d.rowx0 = d.rowbase + d.ny;
             d.rowof = (const uint16_t *)(g + at_rows[m] + align256(rb));
+            // per stored position: y | x << 16, fluid mask, offsets of rows y -/+ 1
+            const std::vector<int32_t> &rw = c->rows[m];
+            const std::vector<uint16_t> &ro = c->rowof[m];
+            auto shift = [&](int y) { return rw[y] - rw[d.ny + y]; };   // rowbase - rowx0
+            std::vector<int4> info(ro.size());
+            for (size_t r = 0; r < ro.size(); ++r) {
+                const int y = ro[r];
+                if (y == 0xFFFF) { info[r] = make_int4(-1, 0, 0, 0); continue; }
+                const int x = rw[d.ny + y] + ((int)r - rw[y]);
+                const int me = shift(y);
+                info[r] = make_int4((int)((uint32_t)y | ((uint32_t)x << 16)), mask[(size_t)y * d.nx + x],
+                                    y > 0 ? shift(y - 1) - me : 0, y < d.ny - 1 ? shift(y + 1) - me : 0);
+            }
+            char *gi = g + at_rows[m] + align256(rb) + align256(ro.size() * 2);
+            LBM_CUDA(c, cudaMemcpy(gi, info.data(), info.size() * sizeof(int4), cudaMemcpyHostToDevice));
+            d.cellinfo = (const int4 *)gi;
         }
         d.ftab = g + at[3 * m + 1];
         d.ztab = g + at[3 * m + 2];
@@ -291,7 +309,9 @@ int build_member(lbm_ctx *c, const lbm_grid *g, const lbm_relax *r, const lbm_fo
     lbm::fastdiv_setup((uint32_t)g->nx, d.nx_mul, d.nx_shr);
     lbm::fastdiv_setup((uint32_t)g->ny, d.ny_mul, d.ny_shr);
     // storage layout: compact fluid rows for pipes whose walls never touch solid cells
-    d.compact = (g->geometry == LBM_PIPE && g->wall != LBM_FULLWAY && rows && rowof) ? 1 : 0;
+    // (positions are packed as 16-bit x and y)
+    d.compact = (g->geometry == LBM_PIPE && g->wall != LBM_FULLWAY && rows && rowof && g->nx <= 0xFFFF &&
+                 g->ny < 0xFFFF) ? 1 : 0;
     d.scells = d.cells;
     d.Ps = d.nx * d.ny;
     if (d.compact) {

@@ -180,6 +180,9 @@ struct Member {
     const int32_t *rowbase;    // compact: [ny] start of row y inside a plane
     const int32_t *rowx0;      // compact: [ny] first fluid x of row y
     const uint16_t *rowof;     // compact: [Ps] row of each stored position (0xFFFF: padding)
+    const int4 *cellinfo;      // compact: [Ps] per stored position: y | x << 16 (all ones:
+                               // padding), the column's fluid mask, and the storage offsets
+                               // of the rows y - 1 and y + 1 at the same x
     int64_t block0;     // first block of this member in a flat launch
     int64_t n_fluid;
     int64_t d2max;      // pipe: fluid iff (2x-nx+1)^2 + (2y-ny+1)^2 <= d2max
@@ -311,14 +314,27 @@ __device__ __forceinline__ bool cell_from_storage(const Member &d, uint32_t sidx
         p.lc = (int32_t)sidx;
         p.di = (int32_t)sidx;
     } else {
+        // one 16-byte table load gives position, fluid mask and row offsets, so the
+        // neighbour addresses of the odd step wait on a single load
         p.z = (int)fastdiv(sidx, d.ps_mul, d.ps_shr);
         const int32_t r = (int32_t)(sidx - (uint32_t)p.z * (uint32_t)d.Ps);
-        const uint16_t y = d.rowof[r];
-        if (y == 0xFFFFu) return false;
-        p.y = y;
-        p.x = d.rowx0[y] + (r - d.rowbase[y]);
+        const int4 ci = d.cellinfo[r];
+        if (ci.x == -1) return false;
+        p.y = ci.x & 0xFFFF;
+        p.x = (int)((uint32_t)ci.x >> 16);
         p.lc = (int32_t)sidx;
         p.di = (p.z * d.ny + p.y) * d.nx + p.x;
+        p.nb = (uint32_t)ci.y;
+        p.ox[0] = -1;
+        p.ox[1] = 0;
+        p.ox[2] = 1;
+        p.oy[0] = ci.z;
+        p.oy[1] = 0;
+        p.oy[2] = ci.w;
+        p.oz[0] = p.z == 0 ? (d.nz - 1) * d.Ps : -d.Ps;
+        p.oz[1] = 0;
+        p.oz[2] = p.z == d.nz - 1 ? -(d.nz - 1) * d.Ps : d.Ps;
+        return (p.nb >> 4) & 1u;
     }
     p.nb = d.colmask[p.y * d.nx + p.x];
     cell_offsets(d, p);
