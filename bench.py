@@ -30,6 +30,7 @@ if ROOT not in sys.path:
 from paper_2405_12082_gb300 import workloads as Wk  # noqa: E402
 
 METRIC = "MLUPS (fluid-cell lattice updates per second) of the D3Q27 MRT pipe step"
+NOMINAL_HBM_GBS = 7900.0      # GB300 HBM3e, nominal
 BYTES_PER_UPDATE = {"f64": 432, "f32": 216, "f16s": 108, "bf16": 108}
 LBM_STEPS_PER_STEP = 100
 
@@ -390,12 +391,15 @@ def run_ours(args):
                      "frac": achieved / peak if achieved else None,
                      "traffic": profiled_traffic(args.precision, args.workload),
                      "kernel": "k_step", "bytes_per_update": bpu, "peak_kind": peak_kind,
-                     "avg_kernel_us": avg_kernel_s * 1e6 if avg_kernel_s else None},
+                     "avg_kernel_us": avg_kernel_s * 1e6 if avg_kernel_s else None,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS if achieved else None,
+                     "nominal_gbs": NOMINAL_HBM_GBS},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
         "n_fluid_cells": n_fluid,
+        "all_cell_mlups": value * sum(cells) / n_fluid,
         "nonfinite_cells": bad,
     }
     print(json.dumps(line), flush=True)
