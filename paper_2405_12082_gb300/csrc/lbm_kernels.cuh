@@ -660,13 +660,30 @@ __device__ __forceinline__ void adjoint_cell(const StepArgs &a, const AdjArgs &j
     const R vx = ux - half * gx, vy = uy - half * gy, vz = uz - half * gz;
     const R base = Arho - (Bx * vx + By * vy + Bz * vz);
 
+    // lambda_i = base + c_i . B + (1 - omega)(cx cy q4 + cx cz q5 + cy cz q6 + (cx^2 - cy^2) q7
+    // + (cx^2 - cz^2) q8), split into one term per axis and the three cross terms; only the
+    // terms with a non-zero lattice coefficient are added
+    const R o4 = om1 * q4, o5 = om1 * q5, o6 = om1 * q6, o7 = om1 * q7, o8 = om1 * q8;
+    const R axm = (o7 + o8) - Bx, axp = (o7 + o8) + Bx;     // cx = -1, +1
+    const R aym = -o7 - By, ayp = By - o7;
+    const R azm = -o8 - Bz, azp = Bz - o8;
     R *lo = static_cast<R *>(j.lam);
     sfor<0, Q>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        R l = base + R(cx) * Bx + R(cy) * By + R(cz) * Bz;
-        l += om1 * (R(cx * cy) * q4 + R(cx * cz) * q5 + R(cy * cz) * q6 + R(cx * cx - cy * cy) * q7 +
-                    R(cx * cx - cz * cz) * q8);
+        R l = base;
+        if constexpr (cx == 1) l += axp;
+        if constexpr (cx == -1) l += axm;
+        if constexpr (cy == 1) l += ayp;
+        if constexpr (cy == -1) l += aym;
+        if constexpr (cz == 1) l += azp;
+        if constexpr (cz == -1) l += azm;
+        if constexpr (cx * cy == 1) l += o4;
+        if constexpr (cx * cy == -1) l -= o4;
+        if constexpr (cx * cz == 1) l += o5;
+        if constexpr (cx * cz == -1) l -= o5;
+        if constexpr (cy * cz == 1) l += o6;
+        if constexpr (cy * cz == -1) l -= o6;
         lo[i * n + lc] = l;
     });
 

@@ -435,6 +435,7 @@ class Lattice:
         if stream is None and torch.cuda.is_available():
             stream = torch.cuda.current_stream().cuda_stream
         self._keep = [force]
+        self.force = force
         if ensemble is not None:
             grids, relaxes, forces = ensemble
             self._keep.append(forces)
@@ -499,3 +500,55 @@ class Lattice:
         E = np.empty((n_sections, len(r_over_R), n_modes + 1))
         lbm_modes(self.ctx, cfg, E)
         return E
+
+
+# ---- autograd wrapper of the adjoint --------------------------------------------------------
+def _autograd_function():
+    import torch
+
+    class PipeObjective(torch.autograd.Function):
+        """J(g_z, omega) of a single half-way pipe over T steps from the lattice's current state
+        (lbm_adjoint): forward sets the per-cell axial acceleration g_z and omega, runs the
+        adjoint call and returns J; backward scales the gradients the call returned.  The
+        lattice advances by T steps."""
+
+        @staticmethod
+        def forward(ctx, gz, omega, lattice, T, objective, checkpoint_every):
+            force = lbm_force.from_buffer_copy(lattice.force if lattice.force is not None else lbm_force())
+            gz_c = gz.detach().contiguous()
+            force.gz_field = gz_c.data_ptr()
+            lbm_set_force(lattice.ctx, force)
+            lattice._keep.append(gz_c)
+            lattice.force = force
+            lbm_set_relax(lattice.ctx, make_relax(float(omega)))
+            dgz = torch.zeros(gz.shape, dtype=torch.float64, device=gz.device)
+            obj = LBM_J_WSS if objective in ("wss", LBM_J_WSS) else LBM_J_UBULK
+            J, dw = lbm_adjoint(lattice.ctx, T, obj, checkpoint_every, dgz)
+            ctx.save_for_backward(dgz)
+            ctx.dw = dw
+            ctx.gz_dtype = gz.dtype
+            ctx.omega_like = omega
+            return torch.tensor(J, dtype=torch.float64, device=gz.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (dgz,) = ctx.saved_tensors
+            g_gz = (gJ * dgz).to(ctx.gz_dtype)
+            om = ctx.omega_like
+            g_om = (gJ * ctx.dw).to(om.dtype).to(om.device) if torch.is_tensor(om) else None
+            return g_gz, g_om, None, None, None, None
+
+    return PipeObjective
+
+
+def pipe_objective(lattice, gz, omega, T, objective="ubulk", checkpoint_every=0):
+    """Differentiable J of the adjoint objectives: J = pipe_objective(L, gz, omega, T) with gz a
+    device tensor of the storage's compute type, shape (nz, ny, nx), and omega a 0-d tensor;
+    J.backward() fills gz.grad and omega.grad from one lbm_adjoint call."""
+    global _PIPE_OBJECTIVE
+    if _PIPE_OBJECTIVE is None:
+        _PIPE_OBJECTIVE = _autograd_function()
+    return _PIPE_OBJECTIVE.apply(gz, omega, lattice, int(T), objective, int(checkpoint_every))
+
+
+_PIPE_OBJECTIVE = None

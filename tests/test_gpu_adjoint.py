@@ -147,3 +147,30 @@ def test_adjoint_rejects_a_trigger(lbm_lib):
         lbm.lbm_adjoint(L.ctx, 4, lbm.LBM_J_UBULK, 0, None)
     assert e.value.status == lbm.LBM_EUNSUPPORTED
     L.close()
+
+
+def test_autograd_wrapper_returns_the_adjoint_gradients(lbm_lib):
+    """pipe_objective(...).backward() hands back exactly what lbm_adjoint computes."""
+    import torch
+    lbm = lbm_lib
+    nx, nz, R, T = 16, 8, 6.5, 30
+    gz0 = Wk.gz_field(nz, nx, nx, base=2e-5, seed=12, rel_amp=0.3)
+    runs = []
+    for mode in ("direct", "autograd"):
+        L = _ctx(lbm, nx, nz, R, 1.3, (0.0, 0.0, 0.0), gz0, "f64")
+        L.init("laminar", noise_amp=1e-4, seed=13)
+        if mode == "direct":
+            d = np.zeros((nz, nx, nx))
+            J, dw = lbm.lbm_adjoint(L.ctx, T, lbm.LBM_J_UBULK, 0, d)
+            runs.append((J, d, dw))
+        else:
+            gz = torch.tensor(gz0, dtype=torch.float64, device="cuda", requires_grad=True)
+            om = torch.tensor(1.3, dtype=torch.float64, requires_grad=True)
+            Jt = lbm.pipe_objective(L, gz, om, T, "ubulk")
+            Jt.backward()
+            runs.append((float(Jt.item()), gz.grad.cpu().numpy(), float(om.grad.item())))
+        L.close()
+    (J0, d0, w0), (J1, d1, w1) = runs
+    assert J0 == J1
+    assert np.array_equal(d0, d1)
+    assert w0 == w1
