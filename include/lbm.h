@@ -241,8 +241,13 @@ int lbm_set_graph(lbm_ctx *ctx, int32_t chunk);
  * blocks per SM; 1 = 256 x 3; 2 = 128 x 8; 3 = 512 x 2; for LBM_F32 also the
  * software-pipelined persistent kernel, 4 = 256 x 3 and 5 = 128 x 6 (each thread
  * copies its next cell's 27 populations into shared memory with cp.async while it
- * computes the current one).  LBM_F64 has one shape (256 x 2).  The arithmetic per
- * cell is the same for every shape. */
+ * computes the current one); 6 = 128 x 8 with each thread taking 2 consecutive planes
+ * of one in-plane position (the default), 7 = the same with 4 planes, 8 = 256 x 4 with
+ * 2 planes.  LBM_F64 has one shape (256 x 2).  The
+ * direct shapes (0-3, 6-8) give bit-identical results; the pipelined kernel is compiled
+ * separately and agrees with them to rounding (the compiler may contract different
+ * multiply-adds).  Errors: LBM_EINVAL (a shape not
+ * available for the storage), LBM_EUNSUPPORTED (an ablation collision model is set). */
 int lbm_set_variant(lbm_ctx *ctx, int32_t variant);
 
 /* Project autotuner for the launch shape: times `steps` steps (2..10000) of every

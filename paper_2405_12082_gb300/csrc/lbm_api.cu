@@ -71,8 +71,8 @@ namespace {
 
 thread_local std::string g_create_error;
 
-// 128 x 8 threads: the fastest shape in sweeps on GB300 (FP64 has a single shape)
-int default_variant(int precision) { return precision == LBM_F64 ? 0 : 2; }
+using lbm::default_variant;
+using lbm::model_variant;
 
 int set_err(lbm_ctx *c, int code, const char *fmt, ...) {
     char buf[512];
@@ -267,7 +267,7 @@ int update_collision(lbm_ctx *c) {
         return set_err(c, LBM_EUNSUPPORTED, "the ablation collision models need F32 or F64 storage");
     if (code != c->collision) {
         c->collision = code;
-        c->variant = default_variant(c->precision);
+        c->variant = code != 0 ? model_variant(c->precision) : default_variant(c->precision);
         drop_graph(c);
     }
     return LBM_OK;
@@ -357,13 +357,16 @@ StepArgs make_args(const lbm_ctx *c, int64_t t) {
     a.dstride = c->dense_total;
     a.collision = c->collision;
     const int bs = lbm::step_threads(c->precision, c->variant);
+    const int zc = lbm::step_zc(c->precision, c->variant);
     int64_t blk = 0;
     for (size_t m = 0; m < c->hm.size(); ++m) {
         const Member &d = c->hm[m];
         a.st[m] = (d.trig && t < d.t_end) ? std::sin(2.0 * M_PI * (double)t / d.period) : 0.0;
         a.stf[m] = (float)a.st[m];
         a.block0[m] = (int32_t)blk;
-        blk += (d.scells + bs - 1) / bs;
+        // threads over (plane group, in-plane position); zc = 1 is every stored cell
+        const int64_t work = (int64_t)d.Ps * ((d.nz + zc - 1) / zc);
+        blk += (work + bs - 1) / bs;
     }
     a.block0[c->hm.size()] = (int32_t)blk;
     a.nblocks_total = (int32_t)blk;
@@ -912,10 +915,10 @@ int lbm_set_graph(lbm_ctx *c, int32_t chunk) {
 
 int lbm_set_variant(lbm_ctx *c, int32_t variant) {
     if (!c) return LBM_EINVAL;
-    if (variant < 0 || variant >= lbm::step_variants(c->precision))
-        return set_err(c, LBM_EINVAL, "launch-shape variant %d out of range (0..%d)", variant,
+    if (!lbm::step_variant_ok(c->precision, variant))
+        return set_err(c, LBM_EINVAL, "launch-shape variant %d is not available for this storage (0..%d)", variant,
                        lbm::step_variants(c->precision) - 1);
-    if (c->collision != 0 && variant != default_variant(c->precision))
+    if (c->collision != 0 && variant != model_variant(c->precision))
         return set_err(c, LBM_EUNSUPPORTED, "the ablation collision models run in the default launch shape only");
     c->variant = variant;
     return LBM_OK;
@@ -962,6 +965,7 @@ int lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *variant, double *best_us) {
     int best = 0, rc = LBM_OK;
     double best_t = 1e300;
     for (int v = 0; v < nv && rc == LBM_OK; ++v) {
+        if (!lbm::step_variant_ok(c->precision, v)) continue;
         c->variant = v;
         c->t = t_save;
         for (int k = 0; k < 2 && rc == LBM_OK; ++k) rc = step_direct(c);
@@ -1212,7 +1216,8 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     if (e == cudaSuccess) e = cudaMalloc(&work, pop_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&mom, (size_t)K * 9 * n * es);
     if (e == cudaSuccess) e = cudaMalloc(&lam, 2 * 27 * n * es);
-    const int64_t nblk = (int64_t)((n + 255) / 256);
+    // adjoint kernel: 256 threads over (plane pair, stored position)
+    const int64_t nblk = ((int64_t)d.Ps * ((d.nz + lbm::ADJ_ZC - 1) / lbm::ADJ_ZC) + 255) / 256;
     const int64_t nslot = nblk * 8;                  // one slot per warp
     if (e == cudaSuccess) e = cudaMalloc((void **)&acc, (nd + 2 * nslot) * sizeof(double));
     auto release = [&]() { cudaFree(ck); cudaFree(work); cudaFree(mom); cudaFree(lam); cudaFree(acc); };
@@ -1235,7 +1240,7 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     const int64_t t0 = c->t;
     // forward pass: a checkpoint at the start of every segment but the last, whose steps
     // store their moments at once (its recompute is skipped in the reverse sweep); the
-    // moment-storing kernel has the 256-thread shape (variant 0)
+    // moment-storing kernel runs in the shape moments_variant
     for (int64_t sgm = 0; sgm < nseg && rc == LBM_OK; ++sgm) {
         const int64_t ns = std::min<int64_t>(K, T - sgm * K);
         if (sgm < nseg - 1) {
@@ -1243,7 +1248,7 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
             if (e != cudaSuccess) { rc = cuda_err(c, e, "checkpoint copy"); break; }
             for (int64_t k = 0; k < ns && rc == LBM_OK; ++k) rc = step_direct(c);
         } else {
-            c->variant = 0;
+            c->variant = lbm::moments_variant(c->precision);
             for (int64_t k = 0; k < ns && rc == LBM_OK; ++k) {
                 StepArgs a = make_args(c, c->t);
                 a.moments = (char *)mom + (size_t)k * 9 * n * es;

@@ -14,16 +14,33 @@ struct ModesArgs {
     double r_over_R[16];
 };
 
-// Launch shapes of the step kernel ("variants"): threads per block and the number of
-// resident blocks per SM the register budget is cut for.  FP64 storage has one shape.
-// Shapes 4 and 5 (F32 storage only) are the software-pipelined persistent kernel.
-struct StepShape { int threads, min_blocks; };
-constexpr StepShape STEP_SHAPES[6] = {{256, 4}, {256, 3}, {128, 8}, {512, 2}, {256, 3}, {128, 6}};
-constexpr StepShape STEP_SHAPE_F64 = {256, 2};
-inline int step_variants(int precision) { return precision == LBM_F64 ? 1 : (precision == LBM_F32 ? 6 : 4); }
+// Launch shapes of the step kernel ("variants"): threads per block, the number of
+// resident blocks per SM the register budget is cut for, and the planes each thread takes
+// (zc).  FP64 storage has one shape.  Shapes 4 and 5 (F32 storage only) are the
+// software-pipelined persistent kernel.
+struct StepShape { int threads, min_blocks, zc, pipelined; };
+constexpr StepShape STEP_SHAPES[9] = {{256, 4, 1, 0}, {256, 3, 1, 0}, {128, 8, 1, 0}, {512, 2, 1, 0},
+                                      {256, 3, 1, 1}, {128, 6, 1, 1}, {128, 8, 2, 0}, {128, 8, 4, 0},
+                                      {256, 4, 2, 0}};
+constexpr StepShape STEP_SHAPE_F64 = {256, 2, 1, 0};
+inline int step_variants(int precision) { return precision == LBM_F64 ? 1 : 9; }
+// 128 x 8 threads, 2 planes per thread: the fastest shape in sweeps on GB300
+inline int default_variant(int precision) { return precision == LBM_F64 ? 0 : 6; }
+// the shape the ablation collision models are compiled for (one plane per thread)
+inline int model_variant(int precision) { return precision == LBM_F64 ? 0 : 2; }
+// the shape of the adjoint's moment-storing recompute (256 threads, 2 planes per thread)
+#ifndef LBM_MOM_VARIANT
+#define LBM_MOM_VARIANT 8
+#endif
+inline int moments_variant(int precision) { return precision == LBM_F64 ? 0 : LBM_MOM_VARIANT; }
+inline bool step_variant_ok(int precision, int variant) {
+    if (variant < 0 || variant >= step_variants(precision)) return false;
+    return precision == LBM_F64 || precision == LBM_F32 || !STEP_SHAPES[variant].pipelined;
+}
 inline int step_threads(int precision, int variant) {
     return precision == LBM_F64 ? STEP_SHAPE_F64.threads : STEP_SHAPES[variant].threads;
 }
+inline int step_zc(int precision, int variant) { return precision == LBM_F64 ? 1 : STEP_SHAPES[variant].zc; }
 
 // Every launcher enqueues on `s` and returns the launch status.
 // Step kernel over all members: a flat grid of a.nblocks_total blocks of
@@ -32,11 +49,16 @@ template <int P>
 cudaError_t launch_step(int wall, int parity, bool stats, const StepArgs &a, int variant, cudaStream_t s);
 
 // Forward step that also stores rho, u, s4..s8 into a.moments (adjoint recompute;
-// single half-way pipe, F32 or F64 storage, 256-thread blocks).
+// single half-way pipe, F32 or F64 storage, in the shape moments_variant).
 template <int P>
 cudaError_t launch_step_moments(int parity, const StepArgs &a, cudaStream_t s);
 
-// One backward step of the adjoint (see k_adjoint).
+// One backward step of the adjoint (see k_adjoint): 256-thread blocks, each thread
+// takes ADJ_ZC consecutive planes of one stored position.
+#ifndef LBM_ADJ_ZC
+#define LBM_ADJ_ZC 2
+#endif
+constexpr int ADJ_ZC = LBM_ADJ_ZC;
 struct AdjArgs {
     const void *lam_next;     // lambda_{t+1}, [27][cells] in the compute type
     void *lam;                // lambda_t (written)

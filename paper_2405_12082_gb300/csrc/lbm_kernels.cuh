@@ -20,17 +20,11 @@ enum { EX_NONE = 0, EX_STATS = 1, EX_MOMENTS = 2 };
 #define LBM_ADJ_MIN_BLOCKS 3
 #endif
 
-template <int P, int PAR, int WALL, int EXTRA, int BS, int MINB, int MODEL = MODEL_MRT_H6>
-__global__ void __launch_bounds__(BS, MINB) k_step(const __grid_constant__ StepArgs a) {
+// Stream, force, collide and store one fluid cell p of member d.
+template <int P, int PAR, int WALL, int EXTRA, int MODEL>
+__device__ __forceinline__ void step_cell(const StepArgs &a, const Member &d, const CellPos &p, int64_t t,
+                                          typename Storage<P>::R stv) {
     using R = typename Storage<P>::R;
-    const int m = find_member(a, blockIdx.x);
-    const Member &d = a.members[m];
-    const uint32_t local = (uint32_t)(blockIdx.x - a.block0[m]) * BS + threadIdx.x;
-    if (local >= (uint32_t)d.scells) return;
-    CellPos p;
-    if (!cell_from_storage(d, local, p)) return;
-    const int64_t t = a.times ? a.times[a.tidx].t : a.t;
-    const R stv = st_of<R>(a, m);
     R v[Q];
     load_pops<P, PAR, WALL>(a, d, p, v);
     R gx, gy, gz;
@@ -59,6 +53,50 @@ __global__ void __launch_bounds__(BS, MINB) k_step(const __grid_constant__ StepA
         }
     }
     store_pops<P, PAR, WALL>(a, d, p, v);
+}
+
+// The cell above p (z + 1) in the same column: same in-plane data, one plane further.
+__device__ __forceinline__ void next_plane(const Member &d, CellPos &p) {
+    p.z += 1;
+    p.lc += d.Ps;
+    p.di += d.nx * d.ny;
+    p.oz[0] = p.z == 0 ? (d.nz - 1) * d.Ps : -d.Ps;
+    p.oz[2] = p.z == d.nz - 1 ? -(d.nz - 1) * d.Ps : d.Ps;
+}
+
+// ZC > 1: each thread takes ZC consecutive planes of one in-plane position (threads of a
+// block stay consecutive in that position, so accesses stay coalesced); the position's
+// table lookup and neighbour offsets are paid once per ZC cells.
+template <int P, int PAR, int WALL, int EXTRA, int BS, int MINB, int MODEL = MODEL_MRT_H6, int ZC = 1>
+__global__ void __launch_bounds__(BS, MINB) k_step(const __grid_constant__ StepArgs a) {
+    using R = typename Storage<P>::R;
+    const int m = find_member(a, blockIdx.x);
+    const Member &d = a.members[m];
+    const uint32_t local = (uint32_t)(blockIdx.x - a.block0[m]) * BS + threadIdx.x;
+    if constexpr (ZC == 1) {
+        if (local >= (uint32_t)d.scells) return;
+        CellPos p;
+        if (!cell_from_storage(d, local, p)) return;
+        const int64_t t = a.times ? a.times[a.tidx].t : a.t;
+        step_cell<P, PAR, WALL, EXTRA, MODEL>(a, d, p, t, st_of<R>(a, m));
+    } else {
+        const uint32_t nzg = (uint32_t)(d.nz + ZC - 1) / ZC;
+        if (local >= (uint32_t)d.Ps * nzg) return;
+        const uint32_t zg = fastdiv(local, d.ps_mul, d.ps_shr);
+        const uint32_t r = local - zg * (uint32_t)d.Ps;
+        CellPos p;
+        if (!cell_from_storage(d, zg * ZC * (uint32_t)d.Ps + r, p)) return;
+        const int64_t t = a.times ? a.times[a.tidx].t : a.t;
+        const R stv = st_of<R>(a, m);
+#pragma unroll 1
+        for (int k = 0; k < ZC; ++k) {
+            if (k > 0) {
+                if (p.z + 1 >= d.nz) break;
+                next_plane(d, p);
+            }
+            step_cell<P, PAR, WALL, EXTRA, MODEL>(a, d, p, t, stv);
+        }
+    }
 }
 
 // ---- software-pipelined persistent step (F32, F64 storage) -----------------------------------
@@ -717,18 +755,34 @@ __device__ __forceinline__ void adjoint_cell(const StepArgs &a, const AdjArgs &j
     j.acc[p.di] += (double)gterm;
 }
 
-// One thread per cell; the objective and dJ/domega terms are summed per block in a fixed
-// order and added to the block's own FP64 slots (deterministic), dJ/dg_z per cell.
+// One thread per ADJ_ZC consecutive planes of one stored position; the objective and
+// dJ/domega terms are summed per warp in a fixed order and added to the warp's own FP64
+// slots (deterministic), dJ/dg_z per cell.
 template <int P, int OBJ>
 __global__ void __launch_bounds__(256, LBM_ADJ_MIN_BLOCKS) k_adjoint(const __grid_constant__ StepArgs a,
                                                                      const AdjArgs j) {
     using R = typename Storage<P>::R;
     const Member &d = a.members[0];
-    const int64_t local = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const uint32_t local = blockIdx.x * 256u + threadIdx.x;
+    const uint32_t nzg = (uint32_t)(d.nz + ADJ_ZC - 1) / ADJ_ZC;
     R x0 = 0, x1 = 0;
-    if (local < d.scells) {
+    if (local < (uint32_t)d.Ps * nzg) {
+        const uint32_t zg = fastdiv(local, d.ps_mul, d.ps_shr);
+        const uint32_t r = local - zg * (uint32_t)d.Ps;
         CellPos p;
-        if (cell_from_storage(d, (uint32_t)local, p)) adjoint_cell<P, OBJ>(a, j, d, p, x0, x1);
+        if (cell_from_storage(d, zg * ADJ_ZC * (uint32_t)d.Ps + r, p)) {
+#pragma unroll 1
+            for (int k = 0; k < ADJ_ZC; ++k) {
+                if (k > 0) {
+                    if (p.z + 1 >= d.nz) break;
+                    next_plane(d, p);
+                }
+                R y0, y1;
+                adjoint_cell<P, OBJ>(a, j, d, p, y0, y1);
+                x0 += y0;
+                x1 += y1;
+            }
+        }
     }
     // warp sums of the objective and omega terms in the compute type, added to the
     // warp's own FP64 slots (fixed order, no block barrier)
@@ -776,11 +830,11 @@ static __global__ void __launch_bounds__(REDUCE_BLOCK) k_sum_columns(const doubl
 
 static inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-template <int P, int BS, int MINB>
+template <int P, int BS, int MINB, int ZC = 1>
 cudaError_t launch_step_shape(int wall, int parity, bool stats, const StepArgs &a, cudaStream_t s) {
     LBM_DISPATCH_WP(wall, parity, {
-        if (stats) k_step<P, PA, W, EX_STATS, BS, MINB><<<a.nblocks_total, BS, 0, s>>>(a);
-        else k_step<P, PA, W, EX_NONE, BS, MINB><<<a.nblocks_total, BS, 0, s>>>(a);
+        if (stats) k_step<P, PA, W, EX_STATS, BS, MINB, MODEL_MRT_H6, ZC><<<a.nblocks_total, BS, 0, s>>>(a);
+        else k_step<P, PA, W, EX_NONE, BS, MINB, MODEL_MRT_H6, ZC><<<a.nblocks_total, BS, 0, s>>>(a);
     });
     return cudaGetLastError();
 }
@@ -864,6 +918,9 @@ cudaError_t launch_step(int wall, int parity, bool stats, const StepArgs &a, int
             case 5:
                 if constexpr (P == LBM_F32) return launch_step_pipe<P, 128, 6>(wall, parity, stats, a, s);
                 else return cudaErrorInvalidValue;
+            case 6: return launch_step_shape<P, 128, 8, 2>(wall, parity, stats, a, s);
+            case 7: return launch_step_shape<P, 128, 8, 4>(wall, parity, stats, a, s);
+            case 8: return launch_step_shape<P, 256, 4, 2>(wall, parity, stats, a, s);
             default: return launch_step_shape<P, 256, 4>(wall, parity, stats, a, s);
         }
     }
@@ -874,8 +931,9 @@ template <int P>
 cudaError_t launch_step_moments(int parity, const StepArgs &a, cudaStream_t s) {
     if constexpr (P == LBM_F64 || P == LBM_F32) {
         constexpr int BS = 256, MINB = (P == LBM_F64) ? 2 : 4;
-        if (parity == 0) k_step<P, 0, LBM_HALFWAY, EX_MOMENTS, BS, MINB><<<a.nblocks_total, BS, 0, s>>>(a);
-        else k_step<P, 1, LBM_HALFWAY, EX_MOMENTS, BS, MINB><<<a.nblocks_total, BS, 0, s>>>(a);
+        constexpr int ZC = (P == LBM_F64) ? 1 : STEP_SHAPES[LBM_MOM_VARIANT].zc;
+        if (parity == 0) k_step<P, 0, LBM_HALFWAY, EX_MOMENTS, BS, MINB, MODEL_MRT_H6, ZC><<<a.nblocks_total, BS, 0, s>>>(a);
+        else k_step<P, 1, LBM_HALFWAY, EX_MOMENTS, BS, MINB, MODEL_MRT_H6, ZC><<<a.nblocks_total, BS, 0, s>>>(a);
         return cudaGetLastError();
     } else {
         return cudaErrorNotSupported;

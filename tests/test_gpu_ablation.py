@@ -107,7 +107,7 @@ def test_switching_models_and_errors(lbm_lib):
     assert e.value.status == lbm.LBM_EINVAL
     lbm.lbm_set_variant(L.ctx, 0)
     lbm.lbm_set_collision(L.ctx, "bgk", "hermite6")
-    assert L.info()["variant"] == 2                    # back to the default shape
+    assert L.info()["variant"] == 2                    # the shape of the ablation kernels
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_set_variant(L.ctx, 1)
     assert e.value.status == lbm.LBM_EUNSUPPORTED

@@ -51,7 +51,7 @@ def _sample(cfg, n, seed):
 @pytest.fixture(scope="module")
 def c2_state(lbm_lib):
     cfg, L, tr = _c2(lbm_lib)
-    assert L.info()["variant"] == 2           # the 128 x 8 launch shape the bench times
+    assert L.info()["variant"] == 6           # the launch shape the bench times (128 x 8, 2 planes per thread)
     L.init("loglaw", noise_amp=cfg["noise"], seed=Wk.SEED)
     f0 = L.populations()
     L.step(1)
