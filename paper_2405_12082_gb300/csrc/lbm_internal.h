@@ -19,20 +19,22 @@ struct ModesArgs {
 // (zc).  FP64 storage has one shape.  Shapes 4 and 5 (F32 storage only) are the
 // software-pipelined persistent kernel.
 struct StepShape { int threads, min_blocks, zc, pipelined; };
-constexpr StepShape STEP_SHAPES[9] = {{256, 4, 1, 0}, {256, 3, 1, 0}, {128, 8, 1, 0}, {512, 2, 1, 0},
-                                      {256, 3, 1, 1}, {128, 6, 1, 1}, {128, 8, 2, 0}, {128, 8, 4, 0},
-                                      {256, 4, 2, 0}};
+constexpr StepShape STEP_SHAPES[11] = {{256, 4, 1, 0}, {256, 3, 1, 0}, {128, 8, 1, 0}, {512, 2, 1, 0},
+                                       {256, 3, 1, 1}, {128, 6, 1, 1}, {128, 8, 2, 0}, {128, 8, 4, 0},
+                                       {256, 4, 2, 0}, {128, 7, 2, 0}, {128, 6, 2, 0}};
 constexpr StepShape STEP_SHAPE_F64 = {256, 2, 1, 0};
-inline int step_variants(int precision) { return precision == LBM_F64 ? 1 : 9; }
-// 128 x 8 threads, 2 planes per thread: the fastest shape in sweeps on GB300
-inline int default_variant(int precision) { return precision == LBM_F64 ? 0 : 6; }
+inline int step_variants(int precision) { return precision == LBM_F64 ? 1 : 11; }
+// the fastest shapes in sweeps on GB300: 128 x 8 threads with 2 planes per thread for
+// F32 storage, with 4 planes for the 16-bit formats
+inline int default_variant(int precision) {
+    return precision == LBM_F64 ? 0 : (precision == LBM_F32 ? 6 : 7);
+}
 // the shape the ablation collision models are compiled for (one plane per thread)
 inline int model_variant(int precision) { return precision == LBM_F64 ? 0 : 2; }
-// the shape of the adjoint's moment-storing recompute (256 threads, 2 planes per thread)
-#ifndef LBM_MOM_VARIANT
-#define LBM_MOM_VARIANT 8
-#endif
-inline int moments_variant(int precision) { return precision == LBM_F64 ? 0 : LBM_MOM_VARIANT; }
+// the shape of the adjoint's moment-storing recompute (256 x 4, one plane per thread:
+// two planes per thread measured 2 % slower there)
+constexpr int MOM_VARIANT = 0;
+inline int moments_variant(int) { return MOM_VARIANT; }
 inline bool step_variant_ok(int precision, int variant) {
     if (variant < 0 || variant >= step_variants(precision)) return false;
     return precision == LBM_F64 || precision == LBM_F32 || !STEP_SHAPES[variant].pipelined;
@@ -54,11 +56,9 @@ template <int P>
 cudaError_t launch_step_moments(int parity, const StepArgs &a, cudaStream_t s);
 
 // One backward step of the adjoint (see k_adjoint): 256-thread blocks, each thread
-// takes ADJ_ZC consecutive planes of one stored position.
-#ifndef LBM_ADJ_ZC
-#define LBM_ADJ_ZC 2
-#endif
-constexpr int ADJ_ZC = LBM_ADJ_ZC;
+// takes ADJ_ZC consecutive planes of one stored position (two planes measured 7 %
+// slower than one on GB300: the loop state spills at the kernel's register budget).
+constexpr int ADJ_ZC = 1;
 struct AdjArgs {
     const void *lam_next;     // lambda_{t+1}, [27][cells] in the compute type
     void *lam;                // lambda_t (written)

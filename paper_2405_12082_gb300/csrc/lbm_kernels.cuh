@@ -921,6 +921,8 @@ cudaError_t launch_step(int wall, int parity, bool stats, const StepArgs &a, int
             case 6: return launch_step_shape<P, 128, 8, 2>(wall, parity, stats, a, s);
             case 7: return launch_step_shape<P, 128, 8, 4>(wall, parity, stats, a, s);
             case 8: return launch_step_shape<P, 256, 4, 2>(wall, parity, stats, a, s);
+            case 9: return launch_step_shape<P, 128, 7, 2>(wall, parity, stats, a, s);
+            case 10: return launch_step_shape<P, 128, 6, 2>(wall, parity, stats, a, s);
             default: return launch_step_shape<P, 256, 4>(wall, parity, stats, a, s);
         }
     }
@@ -931,7 +933,7 @@ template <int P>
 cudaError_t launch_step_moments(int parity, const StepArgs &a, cudaStream_t s) {
     if constexpr (P == LBM_F64 || P == LBM_F32) {
         constexpr int BS = 256, MINB = (P == LBM_F64) ? 2 : 4;
-        constexpr int ZC = (P == LBM_F64) ? 1 : STEP_SHAPES[LBM_MOM_VARIANT].zc;
+        constexpr int ZC = (P == LBM_F64) ? 1 : STEP_SHAPES[MOM_VARIANT].zc;
         if (parity == 0) k_step<P, 0, LBM_HALFWAY, EX_MOMENTS, BS, MINB, MODEL_MRT_H6, ZC><<<a.nblocks_total, BS, 0, s>>>(a);
         else k_step<P, 1, LBM_HALFWAY, EX_MOMENTS, BS, MINB, MODEL_MRT_H6, ZC><<<a.nblocks_total, BS, 0, s>>>(a);
         return cudaGetLastError();

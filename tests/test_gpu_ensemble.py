@@ -89,7 +89,7 @@ def test_launch_shapes_agree(lbm_lib):
     L = lbm.Lattice(grid, relax, force)
     nv = L.info()["n_variants"]
     L.close()
-    assert nv == 9      # direct shapes, two software-pipelined persistent shapes, three with 2 or 4 planes per thread
+    assert nv == 11     # direct shapes, two software-pipelined persistent shapes, five with 2 or 4 planes per thread
     for v in range(nv):
         L = lbm.Lattice(grid, relax, force)
         lbm.lbm_set_variant(L.ctx, v)
@@ -121,7 +121,7 @@ def test_plane_coarsened_shapes_on_ragged_pipes(lbm_lib):
         relaxes = [lbm.lbm_relax(1.3), lbm.lbm_relax(1.6)]
         forces = [lbm.make_force(g=(0, 0, 1e-5)), lbm.make_force(g=(1e-6, 0, 2e-5))]
         ref = None
-        for v in (2, 6, 7, 8):
+        for v in (2, 6, 7, 8, 9, 10):
             E = lbm.Lattice(None, None, ensemble=(grids, relaxes, forces))
             lbm.lbm_set_variant(E.ctx, v)
             lbm.lbm_init(E.ctx, "laminar", noise_amp=1e-3, seed=21)
@@ -152,7 +152,7 @@ def test_autotune_leaves_the_state_untouched(lbm_lib):
     acc0 = np.empty((4, grid.nz, grid.ny, grid.nx))
     c0 = lbm.lbm_stats_get(L.ctx, acc0)
     v, us = lbm.lbm_autotune(L.ctx, 6)
-    assert 0 <= v < 9 and us > 0
+    assert 0 <= v < 11 and us > 0
     info = L.info()
     assert info["t"] == 5 and info["variant"] == v
     assert np.array_equal(_populations(lbm, L.ctx, grid), before)
