@@ -164,6 +164,21 @@ typedef struct {
 int lbm_create(lbm_ctx **out, const lbm_grid *grid, const lbm_relax *relax,
                const lbm_force *force, void *stream);
 
+/* Device-memory hooks for the contexts created after this call (process-wide; a
+ * context keeps the hooks it was created with until lbm_free).  alloc(bytes, stream,
+ * user) returns device memory of at least `bytes` bytes, 256-byte aligned, usable on
+ * `stream` (the context's stream), or NULL; free(ptr, stream, user) releases it.  The
+ * library synchronises the context's stream before it frees anything.  Every device
+ * buffer a context owns (populations, tables, statistics, staging, graph tables, the
+ * adjoint's and the autotuner's temporaries) comes from the hooks; pinned host memory
+ * and events do not.  A NULL result, or one not 256-byte aligned, is reported as
+ * LBM_ENOMEM by the call that needed it.  Both NULL: cudaMalloc / cudaFree (the
+ * default).  Errors: LBM_EINVAL (one hook NULL, the other not).  This serves callers
+ * whose device memory belongs to a pool of their own (a framework's caching allocator). */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*lbm_free_fn)(void *ptr, void *stream, void *user);
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void *user);
+
 /* An ensemble of n independent pipes (1 <= n <= LBM_MAX_MEMBERS) advanced together
  * by one kernel launch per time step.  grids[k], relax[k], force[k] describe member
  * k; all members share precision and wall.  Per-member calls act on the member

@@ -1,6 +1,7 @@
 // lbm_api.cu -- the C ABI of include/lbm.h: contexts, validation, memory, launches.
 #include <algorithm>
 #include <array>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -64,8 +65,43 @@ struct lbm_ctx {
     lbm::StepTime *h_times[2] = {nullptr, nullptr};   // pinned staging, double-buffered
     cudaEvent_t h_done[2] = {nullptr, nullptr};
     int h_next = 0;
+    // device allocator of this context (lbm_set_allocator at creation; NULL: cudaMalloc)
+    lbm_alloc_fn alloc_fn = nullptr;
+    lbm_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
     std::string err;
 };
+
+namespace {
+
+std::mutex g_alloc_mutex;
+lbm_alloc_fn g_alloc_fn = nullptr;
+lbm_free_fn g_free_fn = nullptr;
+void *g_alloc_user = nullptr;
+
+// Device memory of a context: the caller's allocator when one was set, else cudaMalloc.
+// A hook result that is NULL or not 256-byte aligned counts as out of memory.
+cudaError_t dev_alloc(lbm_ctx *c, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    if (!c->alloc_fn) return cudaMalloc(p, bytes);
+    void *q = c->alloc_fn(bytes, (void *)c->stream, c->alloc_user);
+    if (!q) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {
+        c->free_fn(q, (void *)c->stream, c->alloc_user);
+        return cudaErrorMemoryAllocation;
+    }
+    *p = q;
+    return cudaSuccess;
+}
+
+void dev_free(lbm_ctx *c, void *p) {
+    if (!p) return;
+    if (c->free_fn) c->free_fn(p, (void *)c->stream, c->alloc_user);
+    else cudaFree(p);
+}
+
+}  // namespace
 
 namespace {
 
@@ -130,7 +166,7 @@ int build_tables(lbm_ctx *c) {
         at[3 * m + 1] = total; total += align256(3 * ncol * es);
         at[3 * m + 2] = total; total += align256(2 * (size_t)d.nz * es);
     }
-    cudaError_t e = cudaMalloc(&c->geo, total);
+    cudaError_t e = dev_alloc(c, &c->geo, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         c->geo = nullptr;
@@ -397,11 +433,11 @@ int ensure_scratch(lbm_ctx *c, size_t bytes) {
     if (bytes <= c->scratch_bytes) return LBM_OK;
     if (c->scratch) {
         cudaStreamSynchronize(c->stream);
-        cudaFree(c->scratch);
+        dev_free(c, c->scratch);
         c->scratch = nullptr;
         c->scratch_bytes = 0;
     }
-    cudaError_t e = cudaMalloc(&c->scratch, bytes);
+    cudaError_t e = dev_alloc(c, &c->scratch, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_err(c, LBM_ENOMEM, "cannot allocate %zu bytes of staging memory", bytes);
@@ -424,6 +460,12 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
     if (s16 == 0) s16 = 16;
     if (s16 < 1 || s16 > 24) return set_err(nullptr, LBM_EINVAL, "f16_log2_scale must be in 1..24");
     lbm_ctx *c = new lbm_ctx();
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mutex);
+        c->alloc_fn = g_alloc_fn;
+        c->free_fn = g_free_fn;
+        c->alloc_user = g_alloc_user;
+    }
     c->precision = prec;
     c->wall = wall;
     c->variant = default_variant(prec);
@@ -467,14 +509,14 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
     c->mass0.assign(n, 0.0);
     c->mass0_valid.assign(n, false);
     const size_t bytes = (size_t)27 * (size_t)c->stride * c->esize;
-    cudaError_t e = cudaMalloc(&c->pops, bytes);
+    cudaError_t e = dev_alloc(c, &c->pops, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return set_err(nullptr, LBM_ENOMEM, "cannot allocate %zu bytes of populations", bytes);
     }
-    e = cudaMalloc((void **)&c->dm, sizeof(Member) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&c->partials, sizeof(double) * (lbm::REDUCE_MAX_BLOCKS * 5 + 8));
+    e = dev_alloc(c, (void **)&c->dm, sizeof(Member) * n);
+    if (e == cudaSuccess) e = dev_alloc(c, (void **)&c->partials, sizeof(double) * (lbm::REDUCE_MAX_BLOCKS * 5 + 8));
     if (e != cudaSuccess) {
         cudaGetLastError();
         lbm_free(c);
@@ -587,17 +629,29 @@ int lbm_ensemble_create(lbm_ctx **out, int32_t n, const lbm_grid *grids, const l
     return create_common(out, n, grids, relax, force, stream);
 }
 
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void *user) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) {
+        g_create_error = "lbm_set_allocator needs both hooks or neither";
+        return LBM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_alloc_mutex);
+    g_alloc_fn = alloc;
+    g_free_fn = free_fn;
+    g_alloc_user = user;
+    return LBM_OK;
+}
+
 void lbm_free(lbm_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    cudaFree(c->pops);
-    cudaFree(c->dm);
-    cudaFree(c->stats);
-    cudaFree(c->scratch);
-    cudaFree(c->partials);
-    cudaFree(c->geo);
+    dev_free(c, c->pops);
+    dev_free(c, c->dm);
+    dev_free(c, c->stats);
+    dev_free(c, c->scratch);
+    dev_free(c, c->partials);
+    dev_free(c, c->geo);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    cudaFree(c->d_times);
+    dev_free(c, c->d_times);
     for (int b = 0; b < 2; ++b) {
         if (c->h_times[b]) cudaFreeHost(c->h_times[b]);
         if (c->h_done[b]) cudaEventDestroy(c->h_done[b]);
@@ -887,7 +941,7 @@ int lbm_set_graph(lbm_ctx *c, int32_t chunk) {
         return set_err(c, LBM_EINVAL, "graph chunk must be 0 or an even number in 2..4096");
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     drop_graph(c);
-    cudaFree(c->d_times);
+    dev_free(c, c->d_times);
     c->d_times = nullptr;
     for (int b = 0; b < 2; ++b) {
         if (c->h_times[b]) cudaFreeHost(c->h_times[b]);
@@ -898,7 +952,7 @@ int lbm_set_graph(lbm_ctx *c, int32_t chunk) {
     c->graph_chunk = 0;
     if (chunk == 0) return LBM_OK;
     const size_t bytes = sizeof(lbm::StepTime) * chunk;
-    cudaError_t e = cudaMalloc((void **)&c->d_times, bytes);
+    cudaError_t e = dev_alloc(c, (void **)&c->d_times, bytes);
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         e = cudaMallocHost((void **)&c->h_times[b], bytes);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->h_done[b], cudaEventDisableTiming);
@@ -947,7 +1001,7 @@ int lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *variant, double *best_us) {
     const int nv = lbm::step_variants(c->precision);
     const size_t bytes = (size_t)27 * c->stride * c->esize;
     void *save = nullptr;
-    if (cudaMalloc(&save, bytes) != cudaSuccess) {
+    if (dev_alloc(c, &save, bytes) != cudaSuccess) {
         cudaGetLastError();
         return set_err(c, LBM_ENOMEM, "cannot allocate the state copy for autotuning");
     }
@@ -983,7 +1037,7 @@ int lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *variant, double *best_us) {
     cudaStreamSynchronize(c->stream);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(save);
+    dev_free(c, save);
     c->t = t_save;
     c->stats = stats_save;
     c->stats_count = count_save;
@@ -1098,7 +1152,7 @@ int lbm_stats_enable(lbm_ctx *c, int32_t every) {
     if (!c) return LBM_EINVAL;
     if (every < 1) return set_err(c, LBM_EINVAL, "stats interval must be >= 1");
     if (!c->stats) {
-        cudaError_t e = cudaMalloc((void **)&c->stats, sizeof(double) * 4 * c->dense_total);
+        cudaError_t e = dev_alloc(c, (void **)&c->stats, sizeof(double) * 4 * c->dense_total);
         if (e != cudaSuccess) {
             cudaGetLastError();
             c->stats = nullptr;
@@ -1212,15 +1266,15 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     // segment, two adjoint buffers, FP64 accumulators
     void *ck = nullptr, *work = nullptr, *mom = nullptr, *lam = nullptr;
     double *acc = nullptr;
-    cudaError_t e = cudaMalloc(&ck, pop_bytes * (size_t)std::max<int64_t>(nseg - 1, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&work, pop_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&mom, (size_t)K * 9 * n * es);
-    if (e == cudaSuccess) e = cudaMalloc(&lam, 2 * 27 * n * es);
+    cudaError_t e = dev_alloc(c, &ck, pop_bytes * (size_t)std::max<int64_t>(nseg - 1, 1));
+    if (e == cudaSuccess) e = dev_alloc(c, &work, pop_bytes);
+    if (e == cudaSuccess) e = dev_alloc(c, &mom, (size_t)K * 9 * n * es);
+    if (e == cudaSuccess) e = dev_alloc(c, &lam, 2 * 27 * n * es);
     // adjoint kernel: 256 threads over (plane pair, stored position)
     const int64_t nblk = ((int64_t)d.Ps * ((d.nz + lbm::ADJ_ZC - 1) / lbm::ADJ_ZC) + 255) / 256;
     const int64_t nslot = nblk * 8;                  // one slot per warp
-    if (e == cudaSuccess) e = cudaMalloc((void **)&acc, (nd + 2 * nslot) * sizeof(double));
-    auto release = [&]() { cudaFree(ck); cudaFree(work); cudaFree(mom); cudaFree(lam); cudaFree(acc); };
+    if (e == cudaSuccess) e = dev_alloc(c, (void **)&acc, (nd + 2 * nslot) * sizeof(double));
+    auto release = [&]() { dev_free(c, ck); dev_free(c, work); dev_free(c, mom); dev_free(c, lam); dev_free(c, acc); };
     if (e != cudaSuccess) {
         cudaGetLastError();
         release();

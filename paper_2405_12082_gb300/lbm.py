@@ -85,6 +85,11 @@ class lbm_info(ctypes.Structure):
                 ("step_threads", ctypes.c_int32), ("n_variants", ctypes.c_int32), ("graph_chunk", ctypes.c_int32)]
 
 
+# device-memory hooks (lbm_set_allocator)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise RuntimeError("liblbm.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
@@ -130,6 +135,7 @@ def _load():
         "lbm_set_variant": [P, I32],
         "lbm_autotune": [P, I32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
     }
+    sig["lbm_set_allocator"] = [ALLOC_FN, FREE_FN, P]
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
@@ -149,7 +155,7 @@ EXPORTED = ("lbm_create", "lbm_ensemble_create", "lbm_free", "lbm_last_error", "
             "lbm_stats_get", "lbm_modes", "lbm_adjoint", "lbm_profile_enable", "lbm_profile_read",
             "lbm_fluid_mask", "lbm_reduce_static", "lbm_set_graph", "lbm_set_variant", "lbm_autotune",
             "lbm_save", "lbm_load", "lbm_stats_profile", "lbm_dominant_modes", "lbm_transition_matrix",
-            "lbm_mode_correlation", "lbm_set_collision")
+            "lbm_mode_correlation", "lbm_set_collision", "lbm_set_allocator")
 
 
 # ---- marshalling helpers -----------------------------------------------------------------
@@ -552,3 +558,41 @@ def pipe_objective(lattice, gz, omega, T, objective="ubulk", checkpoint_every=0)
 
 
 _PIPE_OBJECTIVE = None
+
+
+# ---- device-memory hooks ---------------------------------------------------------------------
+_ALLOCATOR = None      # the installed callbacks, kept alive while the library may call them
+
+
+def lbm_set_allocator(alloc=None, free=None):
+    """Install Python callables alloc(bytes, stream) -> int address and free(address, stream)
+    as the device allocator of contexts created from now on; no arguments restore
+    cudaMalloc.  Contexts keep the hooks they were created with: keep them installed (or
+    referenced) until those contexts are freed."""
+    global _ALLOCATOR
+    if alloc is None and free is None:
+        _check(None, LIB.lbm_set_allocator(ctypes.cast(None, ALLOC_FN), ctypes.cast(None, FREE_FN), None))
+        return
+
+    def _a(nbytes, stream, user):
+        return int(alloc(int(nbytes), stream or 0))
+
+    def _f(ptr_, stream, user):
+        free(int(ptr_), stream or 0)
+
+    cbs = (ALLOC_FN(_a), FREE_FN(_f))
+    _check(None, LIB.lbm_set_allocator(cbs[0], cbs[1], None))
+    _ALLOCATOR = (cbs, alloc, free, _ALLOCATOR)      # older hooks stay referenced too
+
+
+def use_torch_allocator():
+    """Back every later context's device memory with PyTorch's caching allocator."""
+    import torch
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, torch.cuda.current_device(), stream)
+
+    def free(ptr_, stream):
+        torch.cuda.caching_allocator_delete(ptr_)
+
+    lbm_set_allocator(alloc, free)

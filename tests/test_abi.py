@@ -108,3 +108,13 @@ def test_create_reports_unsupported_sizes_on_the_host(lbm_lib):
         lbm.lbm_create(lbm.make_grid(1000, 1000, 200, 0.0, geometry="box"), lbm.lbm_relax(1.2))
     assert ei.value.status == lbm.LBM_EUNSUPPORTED
     assert "32-bit" in str(ei.value)
+
+
+def test_allocator_hooks_need_both_or_neither(lbm_lib):
+    import ctypes as C
+    lbm = lbm_lib
+    a = lbm.ALLOC_FN(lambda n, s, u: 0)
+    rc = lbm.LIB.lbm_set_allocator(a, C.cast(None, lbm.FREE_FN), None)
+    assert rc == lbm.LBM_EINVAL
+    assert "both" in lbm.lbm_last_error(None)
+    lbm.lbm_set_allocator()           # both NULL: the default, accepted without a GPU
