@@ -35,6 +35,9 @@ def main(argv=None):
     ap.add_argument("--modes-every", type=int, default=20)
     ap.add_argument("--stats-every", type=int, default=100)
     ap.add_argument("--check-every", type=int, default=1000)
+    ap.add_argument("--max-drift", type=float, default=1e-3,
+                    help="stop when the mean density has moved by more than this")
+    ap.add_argument("--wall", default="halfway", choices=["halfway", "bouzidi", "fullway"])
     ap.add_argument("--out", default="run.npz")
     a = ap.parse_args(argv)
 
@@ -44,12 +47,13 @@ def main(argv=None):
     total = a.steps if a.steps > 0 else int(round(a.total * t_let))
     start = max(0, total - int(round(a.window * t_let)))
     start -= start % a.stats_every
-    grid = lbm.make_grid(cfg["nx"], cfg["ny"], cfg["nz"], R, precision=a.precision, wall="halfway")
+    grid = lbm.make_grid(cfg["nx"], cfg["ny"], cfg["nz"], R, precision=a.precision, wall=a.wall)
     trig = Wk.trigger_dict(h=cfg["h"], R=R, nz=cfg["nz"], period=cfg["period"], modes=cfg["trigger_modes"],
                            t_end=cfg["t_trigger"])
     L = lbm.Lattice(grid, lbm.lbm_relax(cfg["omega"]), lbm.make_force(g=(0.0, 0.0, cfg["h"]), trigger=trig))
     L.init("loglaw", noise_amp=cfg["noise"], seed=Wk.SEED)
-    lbm.lbm_set_check(L.ctx, a.check_every, 1e-3)
+    lbm.lbm_set_check(L.ctx, a.check_every, a.max_drift)
+    mass0 = lbm.lbm_reduce(L.ctx)[0]
     mcfg = lbm.make_modes_cfg(cfg["n_sections"], cfg["r_over_R"], cfg["n_theta"], cfg["n_modes"])
     n_samples = (total - start) // a.modes_every
     E = torch.empty((n_samples, cfg["n_sections"], 1, cfg["n_modes"] + 1), dtype=torch.float64, device="cuda")
@@ -91,7 +95,8 @@ def main(argv=None):
     Ub = float(np.mean(ub[len(ub) // 2:])) if ub else float("nan")
     hist = np.bincount(kstar.ravel(), minlength=11)[1:11]
     summary = {
-        "workload": cfg["name"], "precision": a.precision, "steps": total, "stats_from": start,
+        "workload": cfg["name"], "precision": a.precision, "wall": a.wall, "steps": total, "stats_from": start,
+        "mean_density_change": (lbm.lbm_reduce(L.ctx)[0] - mass0) / nf,
         "T_LET": t_let, "Re_tau": us * R / nu, "wall_s": wall,
         "U_b": Ub, "U_b_over_u_star": Ub / us, "Re_bulk": Ub * 2 * R / nu,
         "mode_pdf": (hist / max(hist.sum(), 1)).tolist(),
