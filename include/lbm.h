@@ -258,7 +258,7 @@ int lbm_set_graph(lbm_ctx *ctx, int32_t chunk);
  * copies its next cell's 27 populations into shared memory with cp.async while it
  * computes the current one); 6 = 128 x 8 with each thread taking 2 consecutive planes
  * of one in-plane position (the default for F32 storage), 7 = the same with 4 planes
- * (the default for the 16-bit formats), 8 = 256 x 4, 9 = 128 x 7 and 10 = 128 x 6 with 2
+ * (the default for the 16-bit formats; with LBM_BOUZIDI walls the default is 2), 8 = 256 x 4, 9 = 128 x 7 and 10 = 128 x 6 with 2
  * planes.  LBM_F64 has one shape (256 x 2).  The
  * direct shapes (0-3, 6-10) give bit-identical results; the pipelined kernel is compiled
  * separately and agrees with them to rounding (the compiler may contract different

@@ -153,7 +153,7 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 // trigger-force factors.  Allocated once; the force tables are refilled by set_force.
 int build_tables(lbm_ctx *c) {
     const size_t es = c->precision == LBM_F64 ? 8 : 4;
-    std::vector<size_t> at(c->hm.size() * 3), at_rows(c->hm.size());
+    std::vector<size_t> at(c->hm.size() * 3), at_rows(c->hm.size()), at_delta(c->hm.size());
     size_t total = 0;
     for (size_t m = 0; m < c->hm.size(); ++m) {
         const Member &d = c->hm[m];
@@ -165,6 +165,8 @@ int build_tables(lbm_ctx *c) {
         at[3 * m] = total; total += align256(ncol * 2);
         at[3 * m + 1] = total; total += align256(3 * ncol * es);
         at[3 * m + 2] = total; total += align256(2 * (size_t)d.nz * es);
+        at_delta[m] = total;
+        if (c->wall == LBM_BOUZIDI) total += align256(9 * ncol * es);
     }
     cudaError_t e = dev_alloc(c, &c->geo, total);
     if (e != cudaSuccess) {
@@ -214,6 +216,34 @@ int build_tables(lbm_ctx *c) {
         }
         d.ftab = g + at[3 * m + 1];
         d.ztab = g + at[3 * m + 2];
+        d.dtab = nullptr;
+        if (c->wall == LBM_BOUZIDI) {
+            // Delta = (-b + sqrt(b^2 - a c)) / a of each link from a fluid column to a solid
+            // one (a = |c|^2, b = p . c, c = |p|^2 - R^2, p relative to the axis), in double,
+            // stored in the compute type
+            std::vector<double> dl((size_t)9 * d.nx * d.ny, 0.0);
+            for (int y = 0; y < d.ny; ++y)
+                for (int x = 0; x < d.nx; ++x) {
+                    if (!col_fluid_host(d, x, y)) continue;
+                    const double px = 0.5 * (double)(2 * x - d.nx + 1), py = 0.5 * (double)(2 * y - d.ny + 1);
+                    for (int cy = -1; cy <= 1; ++cy)
+                        for (int cx = -1; cx <= 1; ++cx) {
+                            if ((cx == 0 && cy == 0) || col_fluid_host(d, x + cx, y + cy)) continue;
+                            const double a = (double)(cx * cx + cy * cy);
+                            const double bb = px * cx + py * cy;
+                            const double cc = px * px + py * py - d.R * d.R;
+                            dl[((size_t)y * d.nx + x) * 9 + lbm::nbit(cx, cy)] = (-bb + std::sqrt(bb * bb - a * cc)) / a;
+                        }
+                }
+            char *gd = g + at_delta[m];
+            if (es == 8) {
+                LBM_CUDA(c, cudaMemcpy(gd, dl.data(), dl.size() * 8, cudaMemcpyHostToDevice));
+            } else {
+                std::vector<float> df(dl.begin(), dl.end());
+                LBM_CUDA(c, cudaMemcpy(gd, df.data(), df.size() * 4, cudaMemcpyHostToDevice));
+            }
+            d.dtab = gd;
+        }
     }
     return LBM_OK;
 }
@@ -303,7 +333,7 @@ int update_collision(lbm_ctx *c) {
         return set_err(c, LBM_EUNSUPPORTED, "the ablation collision models need F32 or F64 storage");
     if (code != c->collision) {
         c->collision = code;
-        c->variant = code != 0 ? model_variant(c->precision) : default_variant(c->precision);
+        c->variant = code != 0 ? model_variant(c->precision) : default_variant(c->precision, c->wall);
         drop_graph(c);
     }
     return LBM_OK;
@@ -468,7 +498,7 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
     }
     c->precision = prec;
     c->wall = wall;
-    c->variant = default_variant(prec);
+    c->variant = default_variant(prec, wall);
     c->stream = (cudaStream_t)stream;
     c->f16_scale = std::ldexp(1.0f, s16);
     c->f16_inv = std::ldexp(1.0f, -s16);

@@ -205,6 +205,8 @@ struct Member {
     const uint16_t *colmask;   // [ny][nx] in-plane 3x3 fluid mask of every column (device)
     const void *ftab;          // trigger: [3][ny][nx] column factors (P_x, P_y, P_z), compute type
     const void *ztab;          // trigger: [2][nz] cos, sin of kz 2 pi z / L, compute type
+    const void *dtab;          // Bouzidi walls: [ny][nx][9] wall distance Delta of the link
+                               // (cx, cy) at index nbit(cx, cy), compute type
 };
 
 // Unsigned division by a fixed divisor d >= 1 for n < 2^31 (Granlund-Montgomery with
@@ -380,15 +382,14 @@ __device__ __forceinline__ bool dst_is_fluid(const CellPos &p) {
 template <class R>
 struct BLink { R A, B, C; };
 
+// Delta, the fraction of the link from x to the circle r = R, comes from a per-column
+// table filled on the host (the wall is a cylinder, so it depends on (x, y) and (cx, cy)
+// only).
 template <class R, int J>
 __device__ __forceinline__ BLink<R> bouzidi_link(const Member &d, const CellPos &p) {
     BLink<R> b{R(1), R(0), R(0)};
-    const R px = R(0.5) * R(2 * p.x - d.nx + 1), py = R(0.5) * R(2 * p.y - d.ny + 1);
     constexpr int cx = cx_of(J), cy = cy_of(J);
-    const R a = R(cx * cx + cy * cy);
-    const R bb = px * R(cx) + py * R(cy);
-    const R cc = px * px + py * py - R(d.R) * R(d.R);
-    const R delta = (-bb + sqrt(bb * bb - a * cc)) / a;
+    const R delta = static_cast<const R *>(d.dtab)[(p.y * d.nx + p.x) * 9 + nbit(cx, cy)];
     if (delta >= R(0.5)) {
         b.A = R(1) / (R(2) * delta);
         b.B = (R(2) * delta - R(1)) / (R(2) * delta);
