@@ -233,3 +233,26 @@ def test_taylor_green_decay_is_set_by_the_shear_rates_alone():
         amps.append(np.sum(uu[0, 0] * basis) / np.sum(basis * basis))
     rate = -math.log(amps[1] / amps[0]) / 100
     assert abs(rate / (2 * O.nu_from_omega(omega) * k * k) - 1) < 0.01
+
+
+@pytest.mark.parametrize("R,n", [(7.3, 18), (24.0, 52), (149.5, 300)])
+def test_wall_fraction_lands_on_the_circle(R, n):
+    """For every in-plane link from a fluid column to a solid one, x + Delta c lies on the
+    circle r = R and 0 < Delta <= 1 (the wall crosses the link), Eqs. (fbc1)-(fbc2)."""
+    xc = yc = (n - 1) / 2.0
+    fluid = O.fluid_mask(n, n, 1, R)[0]
+    links = 0
+    for y in range(n):
+        for x in range(n):
+            if not fluid[y, x]:
+                continue
+            for cy in (-1, 0, 1):
+                for cx in (-1, 0, 1):
+                    if (cx, cy) == (0, 0) or fluid[(y + cy) % n, (x + cx) % n]:
+                        continue
+                    px, py = x - xc, y - yc
+                    d = O.wall_fraction(px, py, cx, cy, R)
+                    assert 0.0 < d <= 1.0 + 1e-12
+                    assert abs(math.hypot(px + d * cx, py + d * cy) - R) < 1e-9 * R
+                    links += 1
+    assert links > 0
