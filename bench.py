@@ -1,23 +1,32 @@
 """Throughput of the fused D3Q27 MRT pipe step on one GB300 (JSON line on stdout).
 
-Workload (default): the R = 48 turbulent pipe, 100 x 100 x 480 cells, FP32 shifted
-populations, Re_tau = 181.3 parameters, log-law start with 5 % Gaussian noise, the
-four-mode trigger force active, FP64 statistics every 100 steps and the 16-section
-azimuthal mode analysis every 100 steps.  One bench step = 100 lattice steps (one of
-them with the fused statistics accumulation) + one mode analysis, i.e. every row
-of the hot path.  The population array (518 MB) is larger than L2, so no flush is
-needed between steps.
+Workload (default): the R = 96 pipe, 196 x 196 x 1152 cells (33.4 M fluid cells), FP32
+shifted populations, Re_tau = 181.3 parameters, log-law start with 5 % Gaussian noise,
+the four-mode trigger force active (the flow is still developing inside the timed
+steps), FP64 statistics every 100 steps and the 16-section azimuthal mode analysis once
+per bench step.  One bench step = 100 lattice steps (one of them with the fused
+statistics accumulation) + one mode analysis, i.e. every row of the hot path.  The
+population array (4.8 GB) is larger than L2, so no flush is needed between steps.
+
+The same line also carries, measured in the same run:
+  precisions  the same bench step with F16S and BF16 storage (FP32 collision);
+  adjoint     the adjoint pipe 52 x 52 x 256 (T = 2000, sqrt(T) checkpoints): forward
+              time, adjoint-call time and their ratio;
+  cpu_baseline  the FP64 oracle on a z-slab of the same pipe, on one thread and on
+              every host core (one single-threaded process per core), CPU model named.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c2|c3] [--precision f32|f16s|bf16|f64]
+                  [--workload c3|c2|c4|c5] [--precision f32|f16s|bf16|f64] [--no-extras]
 
 Under torchrun (N > 1) every rank runs its own replica of the pipe on its own GPU
 (the path has no exchange step); rank 0 prints the aggregate.
 `--impl reference` times the FP64 oracle on the host cores instead.
 """
 import argparse
+import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -41,13 +50,14 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"])
+    p.add_argument("--workload", default="c3", choices=["c2", "c3", "c4", "c5"])
     p.add_argument("--graph", type=int, default=None, help="steps per captured graph (0 = direct launches)")
     p.add_argument("--autotune", action="store_true", help="pick the step-kernel launch shape by timing")
     p.add_argument("--variant", type=int, default=None, help="force a step-kernel launch shape")
     p.add_argument("--precision", default="f32", choices=["f32", "f16s", "bf16", "f64"])
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the 16-bit storage and adjoint measurements")
     return p.parse_args()
 
 
@@ -106,45 +116,116 @@ def _oracle_sample(cfg, nz_sample, min_seconds, max_steps):
             "shape": [pp["nx"], pp["ny"], nz_sample]}
 
 
-def oracle_in_child(cfg_name, nz_sample, min_seconds, max_steps):
-    """Runs the oracle sample in a fresh single-threaded interpreter (no GPU context)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
+def _child_env():
+    return dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                CUDA_VISIBLE_DEVICES="")
+
+
+def _child_cmd(cfg_name, nz_sample, min_seconds, max_steps):
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
             "print(json.dumps(bench._oracle_sample(bench.workload(%r), %d, %f, %d)))"
             % (ROOT, cfg_name, nz_sample, min_seconds, max_steps))
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    return [sys.executable, "-c", code]
+
+
+def oracle_in_children(cfg_name, nz_sample, min_seconds, max_steps, n_proc=1):
+    """Runs the oracle sample in n_proc fresh single-threaded interpreters at once (no GPU
+    context in any of them).  Each child times only its own step loop; the aggregate rate
+    is the sum of the children's updates over the longest child time."""
+    procs = [subprocess.Popen(_child_cmd(cfg_name, nz_sample, min_seconds, max_steps), stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=_child_env(), cwd=ROOT)
+             for _ in range(n_proc)]
+    res = []
+    for pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    return {"updates": sum(r["updates"] for r in res), "seconds": max(r["seconds"] for r in res),
+            "steps": min(r["steps"] for r in res), "n_fluid": res[0]["n_fluid"], "shape": res[0]["shape"],
+            "n_proc": n_proc}
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    """CPU model of the host as the OS reports it (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() == "Model name" and v.strip():
+                return v.strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            if k.strip() in ("model name", "CPU part") and v.strip():
+                return v.strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+# z-slab thickness of the oracle sample per workload (bounded CPU work per step)
+SLAB_NZ = {"c2": 16, "c3": 8, "c4": 16, "c5": 16}
+
+
+def slab_text(res):
+    return "%dx%dx%d z-slab (%d fluid cells) of the same pipe" % (tuple(res["shape"]) + (res["n_fluid"],))
 
 
 def cpu_baseline(args, cfg):
-    nz_sample = 48
-    res = oracle_in_child(args.workload, nz_sample, 10.0, 40)
-    val = res["updates"] / res["seconds"] / 1e6
-    return {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "FP64 numpy oracle, %d steps of a %dx%dx%d z-slab of the same pipe (%d fluid cells), "
-                      "one thread" % ((res["steps"],) + tuple(res["shape"]) + (res["n_fluid"],))}
+    """The FP64 oracle timed on the host cores: one thread, then one single-threaded
+    process per core at once (about 10 s each)."""
+    nz = SLAB_NZ[args.workload]
+    one = oracle_in_children(args.workload, nz, 10.0, 60, 1)
+    n = host_cores()
+    allc = oracle_in_children(args.workload, nz, 10.0, 60, n)
+    v1 = one["updates"] / one["seconds"] / 1e6
+    vn = allc["updates"] / allc["seconds"] / 1e6
+    return {"value": vn, "unit": "MLUPS", "cores": n, "kind": "oracle",
+            "sample": "FP64 numpy oracle, %d concurrent single-threaded processes, each >= %d steps of a %s"
+                      % (n, allc["steps"], slab_text(allc)),
+            "single_thread": {"value": v1, "cores": 1, "steps": one["steps"]},
+            "cpu_model": cpu_model(), "nproc": n}
+
+
+def reference_config(cfg, args, res):
+    out = config_json(cfg, args, 1)
+    out["workload"] = "FP64 oracle on a " + slab_text(res) + " of: " + cfg["name"]
+    out["timed_sample"] = {"grid": res["shape"], "n_fluid": res["n_fluid"], "processes": res["n_proc"],
+                           "of_workload": cfg["name"]}
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on every host core (one
+    single-threaded process per core, each stepping its own z-slab of the pipe)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     cfg = workload(args.workload)
-    nz_sample = 16
-    for _ in range(args.warmup):
-        oracle_in_child(args.workload, nz_sample, 0.0, 1)
-    res = oracle_in_child(args.workload, nz_sample, 0.0, max(args.steps, 1))
+    nz = SLAB_NZ[args.workload]
+    n = host_cores()
+    if args.warmup > 0:
+        oracle_in_children(args.workload, nz, 0.0, 1, 1)
+    res = oracle_in_children(args.workload, nz, 0.0, max(args.steps, 1), n)
     val = res["updates"] / res["seconds"] / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * res["seconds"] / res["steps"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_json(cfg, args, 1),
-            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": "%d oracle steps of a %dx%dx%d z-slab per run" % (
-                                 (res["steps"],) + tuple(res["shape"]))},
+            "data": "synthetic", "config": reference_config(cfg, args, res),
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": n, "kind": "oracle",
+                             "sample": "%d concurrent single-threaded processes, %d oracle steps each of a %s"
+                                       % (n, res["steps"], slab_text(res)),
+                             "cpu_model": cpu_model(), "nproc": n},
             "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -208,17 +289,42 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+# the files that define the step kernel: a traffic figure counts only while they are
+# unchanged since the ncu capture that produced it
+KERNEL_SOURCES = ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_staged.cuh", "lbm_internal.h", "lbm_f32.cu",
+                  "lbm_f64.cu", "lbm_f16s.cu", "lbm_bf16.cu")
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2405_12082_gb300", "csrc")
+    for name in KERNEL_SOURCES:
+        path = os.path.join(csrc, name)
+        if os.path.exists(path):
+            h.update(name.encode())
+            h.update(open(path, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(precision, workload_name):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, if any."""
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None
+    when there is none or the kernel sources changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "k_step_%s_%s_traffic.txt" % (precision, workload_name))
+    vals = {}
     try:
         with open(path) as fh:
             for line in fh:
-                if line.startswith("traffic_bytes_per_launch"):
-                    return float(line.split(":")[1])
+                if ":" in line and not line.startswith("#"):
+                    k, _, v = line.partition(":")
+                    vals[k.strip()] = v.strip()
     except Exception:
         return None
-    return None
+    if vals.get("kernel_sources_sha16") != kernel_sources_sha():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except Exception:
+        return None
 
 
 def aggregate_ranks(ms, updates, dist=None, device="cpu"):
@@ -377,6 +483,13 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
+    extras = {}
+    if world == 1 and not args.no_extras and not ensemble:
+        reps = max(1, min(args.steps, 10))
+        extras["precisions"] = {p: measure_precision(lbm, cfg, args, p, reps, 2)
+                                for p in ("f32", "f16s", "bf16") if p != args.precision}
+        extras["adjoint"] = measure_adjoint(lbm, min(reps, 3))
+
     peak, peak_kind = measured_peak()
     avg_kernel_s = (kernel_ms / kernel_launches) * 1e-3 if kernel_launches else None
     bpu = BYTES_PER_UPDATE[args.precision]
@@ -390,6 +503,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None,
                      "traffic": profiled_traffic(args.precision, args.workload),
+                     "kernel_sources_sha16": kernel_sources_sha(),
                      "kernel": "k_step", "bytes_per_update": bpu, "peak_kind": peak_kind,
                      "avg_kernel_us": avg_kernel_s * 1e6 if avg_kernel_s else None,
                      "frac_of_nominal": achieved / NOMINAL_HBM_GBS if achieved else None,
@@ -401,27 +515,72 @@ def run_ours(args):
         "n_fluid_cells": n_fluid,
         "all_cell_mlups": value * sum(cells) / n_fluid,
         "nonfinite_cells": bad,
+        "launch_shape": info["variant"],
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
 
 
-def run_adjoint_bench(args):
-    """Forward MLUPS and the adjoint/forward time ratio on the 52 x 52 x 256, R = 24 pipe
-    (T = 2000 steps, FP32, per-cell axial acceleration): the adjoint call runs its own
-    forward pass with checkpoints, recomputes every segment and sweeps backwards."""
-    import numpy as np
+def measure_precision(lbm, cfg, args, precision, steps, warmup):
+    """The bench step of the workload with another storage precision: G fluid updates/s and
+    the step kernel's mean launch time and roofline fraction (CUDA events)."""
     import torch
-    from paper_2405_12082_gb300 import lbm
+    a = argparse.Namespace(**vars(args))
+    a.precision = precision
+    stream = torch.cuda.current_stream()
+    L = build_single(lbm, cfg, a, stream, 0)
+    n_fluid = L.info()["n_fluid"]
+    mcfg = lbm.make_modes_cfg(cfg["n_sections"], cfg["r_over_R"], cfg["n_theta"], cfg["n_modes"])
+    E = torch.empty((cfg["n_sections"], len(cfg["r_over_R"]), cfg["n_modes"] + 1), dtype=torch.float64,
+                    device="cuda")
+
+    def one_step():
+        lbm.lbm_step(L.ctx, LBM_STEPS_PER_STEP)
+        lbm.lbm_modes(L.ctx, mcfg, E)
+
+    for _ in range(warmup):
+        one_step()
+    torch.cuda.synchronize()
+    lbm.lbm_profile_enable(L.ctx, True)
+    lbm.lbm_profile_read(L.ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kms, kn = lbm.lbm_profile_read(L.ctx)
+    lbm.lbm_profile_enable(L.ctx, False)
+    bad = lbm.lbm_reduce(L.ctx)[4]
+    variant = L.info()["variant"]
+    L.close()
+    peak, _ = measured_peak()
+    bpu = BYTES_PER_UPDATE[precision]
+    avg_s = (kms / kn) * 1e-3 if kn else None
+    achieved = bpu * n_fluid / avg_s / 1e9 if avg_s else None
+    return {"value": n_fluid * LBM_STEPS_PER_STEP * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "steps": steps,
+            "ms_per_step": ms / steps, "bytes_per_update": bpu, "avg_kernel_us": avg_s * 1e6 if avg_s else None,
+            "achieved_gbs": achieved, "frac": achieved / peak if achieved else None, "launch_shape": variant,
+            "nonfinite_cells": bad}
+
+
+def measure_adjoint(lbm, reps, precision="f32", store_all=True):
+    """Forward and adjoint-call times on the adjoint pipe (52 x 52 x 256, R = 24, T = 2000,
+    per-cell axial acceleration, rest start advanced 200 steps): the adjoint call runs its
+    own forward pass with checkpoints every ceil(sqrt(T)) steps, recomputes each segment
+    and sweeps backwards.  Best of `reps` calls each."""
+    import torch
     cfg = workload("c5")
-    prec = args.precision
-    dt = torch.float64 if prec == "f64" else torch.float32
+    dt = torch.float64 if precision == "f64" else torch.float32
     gz = torch.full((cfg["nz"], cfg["ny"], cfg["nx"]), cfg["gz"], dtype=dt, device="cuda")
-    grid = lbm.make_grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["R"], precision=prec, wall="halfway")
+    grid = lbm.make_grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["R"], precision=precision, wall="halfway")
     stream = torch.cuda.current_stream()
     L = lbm.Lattice(grid, lbm.lbm_relax(cfg["omega"]), lbm.make_force(gz_field=gz), stream=stream.cuda_stream)
+    L._keep.append(gz)
     L.init("rest")
     n_fluid = L.info()["n_fluid"]
     T = cfg["T"]
@@ -430,47 +589,48 @@ def run_adjoint_bench(args):
     lbm.lbm_adjoint(L.ctx, 50, lbm.LBM_J_UBULK, 0, dgz)      # warm-up of the adjoint path
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    fwd = []
-    for _ in range(max(args.steps, 1)):
-        e0.record(stream)
-        L.step(T)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fwd.append(e0.elapsed_time(e1))
-    adj = []
-    for _ in range(max(args.steps, 1)):
-        e0.record(stream)
-        J, dw = lbm.lbm_adjoint(L.ctx, T, lbm.LBM_J_UBULK, 0, dgz)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        adj.append(e0.elapsed_time(e1))
-    # the same call with one segment: the forward pass stores the moments of every step
-    # (T x 9 values per stored cell) and nothing is recomputed; timed where memory allows
-    store_all = None
-    es = 8 if prec == "f64" else 4
-    mom_bytes = T * 9 * L.info()["n_cells"] * es
-    if torch.cuda.mem_get_info()[0] > 2 * mom_bytes:
-        sa = []
-        for _ in range(max(args.steps, 1)):
+
+    def timed(fn):
+        best = None
+        for _ in range(max(reps, 1)):
             e0.record(stream)
-            lbm.lbm_adjoint(L.ctx, T, lbm.LBM_J_UBULK, T, dgz)
+            r = fn()
             e1.record(stream)
             torch.cuda.synchronize()
-            sa.append(e0.elapsed_time(e1))
-        store_all = {"adjoint_call_ms": min(sa), "moment_bytes": mom_bytes}
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return best, r
+
+    f_ms, _ = timed(lambda: L.step(T))
+    a_ms, (J, dw) = timed(lambda: lbm.lbm_adjoint(L.ctx, T, lbm.LBM_J_UBULK, 0, dgz))
+    sa = None
+    es = 8 if precision == "f64" else 4
+    mom_bytes = T * 9 * L.info()["n_cells"] * es
+    if store_all and torch.cuda.mem_get_info()[0] > 2 * mom_bytes:
+        s_ms, _ = timed(lambda: lbm.lbm_adjoint(L.ctx, T, lbm.LBM_J_UBULK, T, dgz))
+        sa = {"adjoint_call_ms": s_ms, "moment_bytes": mom_bytes, "reverse_over_forward": (s_ms - f_ms) / f_ms}
     L.close()
-    f_ms, a_ms = min(fwd), min(adj)
-    if store_all is not None:
-        store_all["reverse_over_forward"] = (store_all["adjoint_call_ms"] - f_ms) / f_ms
-    line = {"metric": METRIC + "; adjoint/forward time ratio", "value": n_fluid * T / (f_ms * 1e-3) / 1e6,
-            "unit": "MLUPS", "n_gpus": 1, "steps": len(fwd), "warmup": 1, "ms_per_step": f_ms / T,
+    return {"workload": cfg["name"], "T": T, "precision": precision, "checkpoints": "every ceil(sqrt(T)) steps",
+            "objective": "bulk velocity", "forward_ms": f_ms, "forward_mlups": n_fluid * T / (f_ms * 1e-3) / 1e6,
+            "adjoint_call_ms": a_ms, "reverse_over_forward": (a_ms - f_ms) / f_ms,
+            "total_over_forward": a_ms / f_ms, "J": J, "dJ_domega": dw, "store_all_steps": sa}
+
+
+def run_adjoint_bench(args):
+    """Forward MLUPS and the adjoint/forward time ratio on the 52 x 52 x 256, R = 24 pipe
+    (T = 2000 steps, per-cell axial acceleration): see measure_adjoint."""
+    from paper_2405_12082_gb300 import lbm
+    prec = args.precision
+    adj = measure_adjoint(lbm, max(args.steps, 1), prec)
+    cfg = workload("c5")
+    line = {"metric": METRIC + "; adjoint/forward time ratio", "value": adj["forward_mlups"],
+            "unit": "MLUPS", "n_gpus": 1, "steps": max(args.steps, 1), "warmup": 1,
+            "ms_per_step": adj["forward_ms"] / adj["T"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == "f64" else "f32", "storage": prec, "data": "synthetic (rest start)",
             "config": {"workload": cfg["name"], "grid": [cfg["nx"], cfg["ny"], cfg["nz"]], "R": cfg["R"],
-                       "T": T, "checkpoints": "every ceil(sqrt(T)) steps", "objective": "bulk velocity"},
-            "adjoint": {"forward_ms": f_ms, "adjoint_call_ms": a_ms,
-                        "reverse_over_forward": (a_ms - f_ms) / f_ms, "total_over_forward": a_ms / f_ms,
-                        "J": J, "dJ_domega": dw, "store_all_steps": store_all}}
+                       "T": adj["T"], "checkpoints": adj["checkpoints"], "objective": adj["objective"]},
+            "adjoint": adj}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -189,8 +189,9 @@ int lbm_ensemble_create(lbm_ctx **out, int32_t n, const lbm_grid *grids,
 /* Releases everything the context owns.  NULL-safe.  Synchronises its stream. */
 void lbm_free(lbm_ctx *ctx);
 
-/* Text of the last error of ctx (or of the calling thread's last failed
- * lbm_create / lbm_ensemble_create if ctx is NULL).  Never NULL. */
+/* Text of the last error of ctx (or, if ctx is NULL, of the calling thread's last
+ * failed call that takes no context: lbm_create, lbm_ensemble_create,
+ * lbm_set_allocator, lbm_reduce_static).  Never NULL. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 
 int lbm_set_stream(lbm_ctx *ctx, void *stream);
@@ -259,12 +260,28 @@ int lbm_set_graph(lbm_ctx *ctx, int32_t chunk);
  * computes the current one); 6 = 128 x 8 with each thread taking 2 consecutive planes
  * of one in-plane position (the default for F32 storage), 7 = the same with 4 planes
  * (the default for the 16-bit formats; with LBM_BOUZIDI walls the default is 2), 8 = 256 x 4, 9 = 128 x 7 and 10 = 128 x 6 with 2
- * planes.  LBM_F64 has one shape (256 x 2).  The
- * direct shapes (0-3, 6-10) give bit-identical results; the pipelined kernel is compiled
- * separately and agrees with them to rounding (the compiler may contract different
- * multiply-adds).  Errors: LBM_EINVAL (a shape not
- * available for the storage), LBM_EUNSUPPORTED (an ablation collision model is set). */
+ * planes; 11 and 12 = the staged persistent kernel (512 threads with 3 tiles in flight,
+ * one CTA per SM; 256 threads, 3 tiles, two CTAs per SM): a tile is a group of whole
+ * fluid rows of one plane, whose populations the kernel copies into shared memory with
+ * bulk copies (cp.async.bulk, completing on an mbarrier) several tiles ahead, so loads
+ * are in flight without holding registers; available in every storage for pipes with
+ * half-way or Bouzidi walls whose rows fit its shared-memory segments.  LBM_F64 has shape
+ * 0 (256 x 2) and the staged shapes.  The direct shapes (0-3, 6-10) and the staged shapes
+ * give bit-identical results; the pipelined kernel is compiled separately and agrees
+ * with them to rounding (the compiler may contract different multiply-adds).  Errors:
+ * LBM_EINVAL (a shape not available for the storage), LBM_EUNSUPPORTED (an ablation
+ * collision model is set, or a staged shape the context's walls or rows cannot use). */
 int lbm_set_variant(lbm_ctx *ctx, int32_t variant);
+
+/* Failure-detection tests of the staged shapes (11, 12): the next step launched directly
+ * leaves the copies of staged tile `tile` (0-based, in launch order) unissued, so the CTA
+ * waiting for it gives up after its bounded wait (about 2 s, then about 2 s more for its
+ * copies in flight), records the expiry in the context's device status word and returns
+ * without faulting; that step's results are then incomplete.  The next lbm_reduce or
+ * stability check (lbm_set_check) returns LBM_ETIMEOUT and clears the word; the context
+ * stays usable.  A tile beyond the last one has no effect.  Errors: LBM_EINVAL (tile < 0),
+ * LBM_EUNSUPPORTED (the current shape is not staged). */
+int lbm_test_expire_wait(lbm_ctx *ctx, int32_t tile);
 
 /* Project autotuner for the launch shape: times `steps` steps (2..10000) of every
  * shape on the context's own problem, restores the populations, t and statistics
@@ -302,7 +319,11 @@ int lbm_set_raw(lbm_ctx *ctx, const void *buf, size_t bytes);
  * library's own): lbm_save writes the raw populations, t and the statistics
  * accumulators (if enabled) to `path`; lbm_load restores them into a context created
  * with the same grids, precision and wall (LBM_EINVAL otherwise), so that stepping on
- * gives bit-identical results.  Both synchronise the context's stream. */
+ * gives bit-identical results.  lbm_load checks the whole header against the context
+ * (layout, population bytes, statistics bytes 0 or exactly 4 doubles per cell with an
+ * interval >= 1 and a count >= 0) and reads the whole file into host memory before it
+ * changes anything: a mismatched, corrupt or truncated file returns LBM_EINVAL and
+ * leaves the context as it was.  Both synchronise the context's stream. */
 int lbm_save(lbm_ctx *ctx, const char *path);
 int lbm_load(lbm_ctx *ctx, const char *path);
 
@@ -409,9 +430,10 @@ int lbm_fluid_mask(lbm_ctx *ctx, uint8_t *mask);
  * kernels overlap on the GPU race: order them (one stream).  Asynchronous on
  * `stream` (a cudaStream_t, NULL = default stream).
  * Errors: LBM_EINVAL (NULL pointer, n_cells < 1 or above LBM_STATIC_REDUCE_MAX_CELLS,
- * unknown precision or scale, out not device memory), LBM_ECUDA (no current device,
- * symbol lookup or launch failure).  Calls no cudaMalloc, cudaFree or other
- * allocating routine. */
+ * unknown precision or scale, pops or out neither device nor managed memory),
+ * LBM_ECUDA (no current device, symbol lookup or launch failure); the reason is
+ * reported by lbm_last_error(NULL) in the calling thread.  Calls no cudaMalloc,
+ * cudaFree or other allocating routine. */
 #define LBM_STATIC_REDUCE_MAX_BLOCKS 1216
 #define LBM_STATIC_REDUCE_MAX_CELLS  159072862   /* floor((2^32 - 1) / 27) */
 int lbm_reduce_static(const void *pops, int32_t precision, int32_t f16_log2_scale, int64_t n_cells,

@@ -65,6 +65,9 @@ def build(force=False, verbose=False, extra_flags=()):
             sys.stdout.write(r.stdout + r.stderr)
         return obj
 
+    # the kernel units are the long ones: start them first
+    srcs.sort(key=lambda f: (os.path.getsize(f) > 200 and "lbm_" in os.path.basename(f) and
+                             os.path.basename(f)[4:7] in ("f32", "f64", "f16", "bf1", "sta")), reverse=True)
     with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"

@@ -42,6 +42,8 @@ struct lbm_ctx {
     size_t scratch_bytes = 0;
     double *partials = nullptr;      // reduction partials + final (device)
     void *geo = nullptr;             // column masks and trigger tables of every member (device)
+    int32_t *flags = nullptr;        // device status word of the step kernels (0 = fine)
+    int32_t skip_tile = -1;          // lbm_test_expire_wait: tile of the next staged step left unissued
     int64_t check_every = 0;
     double max_drift = 0;
     std::vector<double> mass0;
@@ -104,8 +106,12 @@ void dev_free(lbm_ctx *c, void *p) {
 }  // namespace
 
 namespace {
-
 thread_local std::string g_create_error;
+}  // namespace
+
+void lbm::set_thread_error(const char *msg) { g_create_error = msg ? msg : ""; }
+
+namespace {
 
 using lbm::default_variant;
 using lbm::model_variant;
@@ -151,9 +157,42 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 // Device tables of every member: the 3x3 in-plane fluid mask of each column and the
 // trigger-force factors.  Allocated once; the force tables are refilled by set_force.
+// Row groups of a compact member for the staged shapes: consecutive fluid rows [y0, y1]
+// such that the rows shifted by -1, 0 and +1 each fit `cap` storage elements; per group
+// two int4 (y0, y1, lo[0], lo[1]), (lo[2], hi[0], hi[1], hi[2]) with lo[s] =
+// rowbase(y0 + s - 1), hi[s] = rowbase(y1 + s).  Empty when a single row does not fit.
+std::vector<int4> row_groups(const Member &d, const std::vector<int32_t> &rows, int cap) {
+    std::vector<int4> out;
+    auto rb = [&](int y) { return y >= d.ny ? d.Ps : rows[y]; };
+    auto span = [&](int y) { return rb(y + 1) - rb(y); };
+    int first = -1, last = -1;
+    for (int y = 0; y < d.ny; ++y)
+        if (span(y) > 0) {
+            if (first < 0) first = y;
+            last = y;
+        }
+    if (first < 1 || last > d.ny - 2) return out;     // a pipe keeps a solid margin
+    auto fits = [&](int y0, int y1) {
+        for (int s = -1; s <= 1; ++s)
+            if (rb(y1 + 1 + s) - rb(y0 + s) > cap) return false;
+        return true;
+    };
+    for (int y = first; y <= last;) {
+        if (!fits(y, y)) return std::vector<int4>();
+        int y1 = y;
+        while (y1 + 1 <= last && fits(y, y1 + 1)) ++y1;
+        out.push_back(make_int4(y, y1, rb(y - 1), rb(y)));
+        out.push_back(make_int4(rb(y + 1), rb(y1), rb(y1 + 1), rb(y1 + 2)));
+        y = y1 + 1;
+    }
+    return out;
+}
+
 int build_tables(lbm_ctx *c) {
     const size_t es = c->precision == LBM_F64 ? 8 : 4;
     std::vector<size_t> at(c->hm.size() * 3), at_rows(c->hm.size()), at_delta(c->hm.size());
+    std::vector<size_t> at_sg(c->hm.size() * 2);
+    std::vector<std::vector<int4>> sg(c->hm.size() * 2);
     size_t total = 0;
     for (size_t m = 0; m < c->hm.size(); ++m) {
         const Member &d = c->hm[m];
@@ -166,7 +205,12 @@ int build_tables(lbm_ctx *c) {
         at[3 * m + 1] = total; total += align256(3 * ncol * es);
         at[3 * m + 2] = total; total += align256(2 * (size_t)d.nz * es);
         at_delta[m] = total;
-        if (c->wall == LBM_BOUZIDI) total += align256(9 * ncol * es);
+        if (c->wall == LBM_BOUZIDI) total += align256(27 * ncol * es);
+        for (int k = 0; k < 2; ++k) {
+            if (d.compact) sg[2 * m + k] = row_groups(d, c->rows[m], lbm::staged_cap(c->precision, k));
+            at_sg[2 * m + k] = total;
+            total += align256(sg[2 * m + k].size() * sizeof(int4));
+        }
     }
     cudaError_t e = dev_alloc(c, &c->geo, total);
     if (e != cudaSuccess) {
@@ -214,14 +258,25 @@ int build_tables(lbm_ctx *c) {
             LBM_CUDA(c, cudaMemcpy(gi, info.data(), info.size() * sizeof(int4), cudaMemcpyHostToDevice));
             d.cellinfo = (const int4 *)gi;
         }
+        for (int k = 0; k < 2; ++k) {
+            const std::vector<int4> &grp = sg[2 * m + k];
+            d.sg[k] = nullptr;
+            d.nsg[k] = (int32_t)(grp.size() / 2);
+            if (!grp.empty()) {
+                LBM_CUDA(c, cudaMemcpy(g + at_sg[2 * m + k], grp.data(), grp.size() * sizeof(int4),
+                                       cudaMemcpyHostToDevice));
+                d.sg[k] = (const int4 *)(g + at_sg[2 * m + k]);
+            }
+        }
         d.ftab = g + at[3 * m + 1];
         d.ztab = g + at[3 * m + 2];
         d.dtab = nullptr;
         if (c->wall == LBM_BOUZIDI) {
             // Delta = (-b + sqrt(b^2 - a c)) / a of each link from a fluid column to a solid
             // one (a = |c|^2, b = p . c, c = |p|^2 - R^2, p relative to the axis), in double,
-            // stored in the compute type
-            std::vector<double> dl((size_t)9 * d.nx * d.ny, 0.0);
+            // and the link coefficients A, B, C of Eqs. (fbc1)-(fbc2), stored in the compute
+            // type (half-way values 1, 0, 0 where no second fluid point exists)
+            std::vector<double> dl((size_t)27 * d.nx * d.ny, 0.0);
             for (int y = 0; y < d.ny; ++y)
                 for (int x = 0; x < d.nx; ++x) {
                     if (!col_fluid_host(d, x, y)) continue;
@@ -232,7 +287,19 @@ int build_tables(lbm_ctx *c) {
                             const double a = (double)(cx * cx + cy * cy);
                             const double bb = px * cx + py * cy;
                             const double cc = px * px + py * py - d.R * d.R;
-                            dl[((size_t)y * d.nx + x) * 9 + lbm::nbit(cx, cy)] = (-bb + std::sqrt(bb * bb - a * cc)) / a;
+                            const double delta = (-bb + std::sqrt(bb * bb - a * cc)) / a;
+                            double A = 1.0, B = 0.0, C = 0.0;
+                            if (delta >= 0.5) {
+                                A = 1.0 / (2.0 * delta);
+                                B = (2.0 * delta - 1.0) / (2.0 * delta);
+                            } else if (col_fluid_host(d, x - cx, y - cy)) {
+                                A = 2.0 * delta;
+                                C = 1.0 - 2.0 * delta;
+                            }
+                            double *t = &dl[(((size_t)y * d.nx + x) * 9 + lbm::nbit(cx, cy)) * 3];
+                            t[0] = A;
+                            t[1] = B;
+                            t[2] = C;
                         }
                 }
             char *gd = g + at_delta[m];
@@ -424,15 +491,26 @@ StepArgs make_args(const lbm_ctx *c, int64_t t) {
     a.collision = c->collision;
     const int bs = lbm::step_threads(c->precision, c->variant);
     const int zc = lbm::step_zc(c->precision, c->variant);
+    const int sk = lbm::staged_of(c->variant);
+    a.err = c->flags;
+    a.skip_tile = -1;
+    if (sk >= 0) {
+        a.stage_cap = lbm::staged_cap(c->precision, sk);
+        a.sg_sel = sk;
+    }
     int64_t blk = 0;
     for (size_t m = 0; m < c->hm.size(); ++m) {
         const Member &d = c->hm[m];
         a.st[m] = (d.trig && t < d.t_end) ? std::sin(2.0 * M_PI * (double)t / d.period) : 0.0;
         a.stf[m] = (float)a.st[m];
         a.block0[m] = (int32_t)blk;
-        // threads over (plane group, in-plane position); zc = 1 is every stored cell
-        const int64_t work = (int64_t)d.Ps * ((d.nz + zc - 1) / zc);
-        blk += (work + bs - 1) / bs;
+        if (sk >= 0) {
+            blk += (int64_t)d.nsg[sk] * d.nz;        // staged: one tile per (plane, row group)
+        } else {
+            // threads over (plane group, in-plane position); zc = 1 is every stored cell
+            const int64_t work = (int64_t)d.Ps * ((d.nz + zc - 1) / zc);
+            blk += (work + bs - 1) / bs;
+        }
     }
     a.block0[c->hm.size()] = (int32_t)blk;
     a.nblocks_total = (int32_t)blk;
@@ -475,6 +553,8 @@ int ensure_scratch(lbm_ctx *c, size_t bytes) {
     c->scratch_bytes = bytes;
     return LBM_OK;
 }
+
+int prepare_variant(lbm_ctx *c);
 
 int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_relax *relax,
                   const lbm_force *force, void *stream) {
@@ -547,6 +627,8 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
     }
     e = dev_alloc(c, (void **)&c->dm, sizeof(Member) * n);
     if (e == cudaSuccess) e = dev_alloc(c, (void **)&c->partials, sizeof(double) * (lbm::REDUCE_MAX_BLOCKS * 5 + 8));
+    if (e == cudaSuccess) e = dev_alloc(c, (void **)&c->flags, 256);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flags, 0, 256, c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         lbm_free(c);
@@ -565,6 +647,7 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
     }
     rc = build_tables(c);
     if (rc == LBM_OK) rc = upload_members(c);
+    if (rc == LBM_OK) rc = prepare_variant(c);
     for (size_t m = 0; rc == LBM_OK && m < c->hm.size(); ++m) rc = fill_force_tables(c, (int)m);
     if (rc) {
         g_create_error = c->err;
@@ -586,6 +669,33 @@ int dispatch(lbm_ctx *c, F &&f) {
     }
     if (e != cudaSuccess) return cuda_err(c, e, "kernel launch");
     c->launches++;
+    return LBM_OK;
+}
+
+// Whether the context can run launch shape `variant`: a staged shape needs compact pipe
+// members whose row groups fit its segments and the default collision model.
+bool variant_available(const lbm_ctx *c, int variant) {
+    if (!lbm::step_variant_ok(c->precision, variant)) return false;
+    const int sk = lbm::staged_of(variant);
+    if (sk < 0) return true;
+    if (c->wall == LBM_FULLWAY || c->collision != 0) return false;
+    for (const Member &d : c->hm)
+        if (!d.compact || d.nsg[sk] < 1) return false;
+    return true;
+}
+
+// Configures the kernels of the context's launch shape (shared-memory size of the staged
+// kernels) ahead of any launch or graph capture.
+int prepare_variant(lbm_ctx *c) {
+    if (lbm::staged_of(c->variant) < 0) return LBM_OK;
+    cudaError_t e = cudaSuccess;
+    switch (c->precision) {
+        case LBM_F64: e = lbm::prepare_step<LBM_F64>(c->wall, c->variant); break;
+        case LBM_F32: e = lbm::prepare_step<LBM_F32>(c->wall, c->variant); break;
+        case LBM_F16S: e = lbm::prepare_step<LBM_F16S>(c->wall, c->variant); break;
+        default: e = lbm::prepare_step<LBM_BF16>(c->wall, c->variant); break;
+    }
+    if (e != cudaSuccess) return cuda_err(c, e, "configuring the staged step kernels");
     return LBM_OK;
 }
 
@@ -612,7 +722,19 @@ int reduce_member(lbm_ctx *c, int m, double *host_out) {
     return LBM_OK;
 }
 
+// The step kernels' status word: a bounded wait that expired is reported once.
+int check_flags(lbm_ctx *c) {
+    int32_t f = 0;
+    LBM_CUDA(c, cudaMemcpyAsync(&f, c->flags, sizeof f, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (f == 0) return LBM_OK;
+    LBM_CUDA(c, cudaMemsetAsync(c->flags, 0, sizeof f, c->stream));
+    return set_err(c, LBM_ETIMEOUT, "a step kernel's bounded wait for its staged tile expired (status %d)", f);
+}
+
 int stability_check(lbm_ctx *c) {
+    int frc = check_flags(c);
+    if (frc) return frc;
     for (size_t m = 0; m < c->hm.size(); ++m) {
         double r[5];
         int rc = reduce_member(c, (int)m, r);
@@ -680,6 +802,7 @@ void lbm_free(lbm_ctx *c) {
     dev_free(c, c->scratch);
     dev_free(c, c->partials);
     dev_free(c, c->geo);
+    dev_free(c, c->flags);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     dev_free(c, c->d_times);
     for (int b = 0; b < 2; ++b) {
@@ -817,6 +940,15 @@ int lbm_init_fields(lbm_ctx *c, const double *rho, const double *u) {
     return LBM_OK;
 }
 
+int lbm_test_expire_wait(lbm_ctx *c, int32_t tile) {
+    if (!c) return LBM_EINVAL;
+    if (lbm::staged_of(c->variant) < 0)
+        return set_err(c, LBM_EUNSUPPORTED, "the current launch shape has no staged tiles");
+    if (tile < 0) return set_err(c, LBM_EINVAL, "tile must be >= 0");
+    c->skip_tile = tile;
+    return LBM_OK;
+}
+
 int lbm_set_check(lbm_ctx *c, int64_t every, double max_mass_drift) {
     if (!c) return LBM_EINVAL;
     if (every < 0 || !(max_mass_drift >= 0)) return set_err(c, LBM_EINVAL, "bad check parameters");
@@ -832,7 +964,11 @@ namespace {
 // One step by a direct launch.
 int step_direct(lbm_ctx *c) {
     const bool stats = c->stats && c->stats_every > 0 && (c->t % c->stats_every == 0);
-    const StepArgs a = make_args(c, c->t);
+    StepArgs a = make_args(c, c->t);
+    if (c->skip_tile >= 0 && lbm::staged_of(c->variant) >= 0) {
+        a.skip_tile = c->skip_tile;
+        c->skip_tile = -1;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->prof) {
         int rc = event_pair(c, e0, e1);
@@ -864,6 +1000,8 @@ void drop_graph(lbm_ctx *c) {
 // phase from d_times[k], so one instantiated graph serves every replay.
 int build_graph(lbm_ctx *c) {
     drop_graph(c);
+    int prc = prepare_variant(c);
+    if (prc) return prc;
     const int every = (c->stats && c->stats_every > 0) ? c->stats_every : 0;
     cudaStream_t cs;
     LBM_CUDA(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -1004,8 +1142,15 @@ int lbm_set_variant(lbm_ctx *c, int32_t variant) {
                        lbm::step_variants(c->precision) - 1);
     if (c->collision != 0 && variant != model_variant(c->precision))
         return set_err(c, LBM_EUNSUPPORTED, "the ablation collision models run in the default launch shape only");
+    if (!variant_available(c, variant))
+        return set_err(c, LBM_EUNSUPPORTED,
+                       "launch shape %d (staged) needs pipes with half-way or Bouzidi walls whose rows fit %d "
+                       "elements per segment", variant, lbm::staged_cap(c->precision, std::max(0, lbm::staged_of(variant))));
+    const int old = c->variant;
     c->variant = variant;
-    return LBM_OK;
+    const int rc = prepare_variant(c);
+    if (rc) c->variant = old;
+    return rc;
 }
 
 int lbm_set_collision(lbm_ctx *c, int32_t model, int32_t equilibrium) {
@@ -1049,8 +1194,10 @@ int lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *variant, double *best_us) {
     int best = 0, rc = LBM_OK;
     double best_t = 1e300;
     for (int v = 0; v < nv && rc == LBM_OK; ++v) {
-        if (!lbm::step_variant_ok(c->precision, v)) continue;
+        if (!variant_available(c, v)) continue;
         c->variant = v;
+        rc = prepare_variant(c);
+        if (rc) break;
         c->t = t_save;
         for (int k = 0; k < 2 && rc == LBM_OK; ++k) rc = step_direct(c);
         if (rc) break;
@@ -1175,7 +1322,9 @@ int lbm_set_raw(lbm_ctx *c, const void *buf, size_t bytes) {
 
 int lbm_reduce(lbm_ctx *c, double *out) {
     if (!c || !out) return LBM_EINVAL;
-    return reduce_member(c, c->sel, out);
+    const int rc = reduce_member(c, c->sel, out);
+    if (rc) return rc;
+    return check_flags(c);
 }
 
 int lbm_stats_enable(lbm_ctx *c, int32_t every) {
@@ -1499,36 +1648,37 @@ int lbm_load(lbm_ctx *c, const char *path) {
     if (!fp) return set_err(c, LBM_EINVAL, "cannot open %s", path);
     FileHeader h;
     bool ok = std::fread(&h, sizeof h, 1, fp) == 1 && std::memcmp(h.magic, "LBMCKPT1", 8) == 0;
-    if (!ok || !same_layout(c, h) || h.pop_bytes != (int64_t)27 * c->stride * (int64_t)c->esize) {
+    // the header must describe exactly this context's buffers before anything is read
+    // into them: the population bytes of this layout, and either no statistics or
+    // 4 FP64 sums per dense cell with a sampling interval >= 1 and a count >= 0
+    const int64_t pop_need = (int64_t)27 * c->stride * (int64_t)c->esize;
+    const int64_t stats_need = (int64_t)sizeof(double) * 4 * c->dense_total;
+    if (!ok || !same_layout(c, h) || h.pop_bytes != pop_need ||
+        (h.stats_bytes != 0 && (h.stats_bytes != stats_need || h.stats_every < 1 || h.stats_count < 0)) ||
+        h.t < 0) {
         std::fclose(fp);
         return set_err(c, LBM_EINVAL, "%s is not a checkpoint of a context with this layout", path);
     }
-    std::vector<char> host((size_t)std::max<int64_t>(h.pop_bytes, h.stats_bytes));
-    ok = std::fread(host.data(), 1, (size_t)h.pop_bytes, fp) == (size_t)h.pop_bytes;
-    cudaError_t e = cudaSuccess;
-    if (ok) {
-        e = cudaMemcpyAsync(c->pops, host.data(), (size_t)h.pop_bytes, cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    // read the whole file into host memory first; the context changes only once all
+    // of it has been read
+    std::vector<char> pops((size_t)h.pop_bytes), stats((size_t)h.stats_bytes);
+    ok = std::fread(pops.data(), 1, pops.size(), fp) == pops.size() &&
+         std::fread(stats.data(), 1, stats.size(), fp) == stats.size();
+    std::fclose(fp);
+    if (!ok) return set_err(c, LBM_EINVAL, "reading %s failed (file truncated)", path);
+    if (h.stats_bytes && !c->stats) {
+        int rc = lbm_stats_enable(c, h.stats_every);
+        if (rc) return rc;
     }
-    if (ok && e == cudaSuccess && h.stats_bytes) {
-        if (!c->stats) {
-            std::fclose(fp);
-            int rc = lbm_stats_enable(c, h.stats_every);
-            if (rc) return rc;
-            fp = std::fopen(path, "rb");
-            ok = fp && std::fseek(fp, (long)(sizeof h + h.pop_bytes), SEEK_SET) == 0;
-        }
-        ok = ok && std::fread(host.data(), 1, (size_t)h.stats_bytes, fp) == (size_t)h.stats_bytes;
-        if (ok) {
-            e = cudaMemcpyAsync(c->stats, host.data(), (size_t)h.stats_bytes, cudaMemcpyHostToDevice, c->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        }
+    cudaError_t e = cudaMemcpyAsync(c->pops, pops.data(), pops.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && h.stats_bytes)
+        e = cudaMemcpyAsync(c->stats, stats.data(), stats.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "checkpoint upload");
+    if (h.stats_bytes) {
         c->stats_every = h.stats_every;
         c->stats_count = h.stats_count;
     }
-    if (fp) std::fclose(fp);
-    if (e != cudaSuccess) return cuda_err(c, e, "checkpoint upload");
-    if (!ok) return set_err(c, LBM_EINVAL, "reading %s failed", path);
     c->t = h.t;
     for (size_t m = 0; m < c->hm.size(); ++m) c->mass0_valid[m] = false;
     return LBM_OK;

@@ -53,6 +53,12 @@ __host__ __device__ constexpr int opp_of(int i) {
 __host__ __device__ constexpr double w_of(int i) {
     return i == 0 ? 8.0 / 27.0 : (i <= 6 ? 2.0 / 27.0 : (i <= 18 ? 1.0 / 54.0 : 1.0 / 216.0));
 }
+// index of the velocity (cx, cy, cz)
+__host__ __device__ constexpr int dir_of(int cx, int cy, int cz) {
+    for (int j = 0; j < 27; ++j)
+        if (cx_of(j) == cx && cy_of(j) == cy && cz_of(j) == cz) return j;
+    return -1;
+}
 // in-plane neighbourhood bit of (cx, cy): bit (cy + 1) * 3 + (cx + 1)
 __host__ __device__ constexpr int nbit(int cx, int cy) { return (cy + 1) * 3 + (cx + 1); }
 
@@ -205,8 +211,12 @@ struct Member {
     const uint16_t *colmask;   // [ny][nx] in-plane 3x3 fluid mask of every column (device)
     const void *ftab;          // trigger: [3][ny][nx] column factors (P_x, P_y, P_z), compute type
     const void *ztab;          // trigger: [2][nz] cos, sin of kz 2 pi z / L, compute type
-    const void *dtab;          // Bouzidi walls: [ny][nx][9] wall distance Delta of the link
+    const void *dtab;          // Bouzidi walls: [ny][nx][9][3] coefficients A, B, C of the link
                                // (cx, cy) at index nbit(cx, cy), compute type
+    const int4 *sg[2];         // compact: row groups of the two staged launch shapes (2 int4
+                               // per group, see lbm_staged.cuh), nsg[k] groups (0: shape
+                               // not available for this member)
+    int32_t nsg[2];
 };
 
 // Unsigned division by a fixed divisor d >= 1 for n < 2^31 (Granlund-Montgomery with
@@ -249,6 +259,11 @@ struct StepArgs {
     int32_t tidx;
     void *moments;            // adjoint recompute: [9][cells] rho, u, s4..s8 of member 0
     int32_t collision;        // collision model (MODEL_* bits), the same for every member
+    int32_t stage_cap;        // staged shapes: storage elements per direction segment
+    int32_t sg_sel;           // staged shapes: which row-group table (0 or 1)
+    int32_t *err;             // device status word (bounded waits that expired), or NULL
+    int32_t skip_tile;        // failure-detection tests: a staged tile whose copies are never
+                              // issued (its wait expires); -1 otherwise
 };
 
 __device__ __forceinline__ int find_member(const StepArgs &a, int blk) {
@@ -382,22 +397,33 @@ __device__ __forceinline__ bool dst_is_fluid(const CellPos &p) {
 template <class R>
 struct BLink { R A, B, C; };
 
-// Delta, the fraction of the link from x to the circle r = R, comes from a per-column
-// table filled on the host (the wall is a cylinder, so it depends on (x, y) and (cx, cy)
-// only).
+// The coefficients come from a per-column table filled on the host in FP64 from Delta,
+// the fraction of the link from x to the circle r = R (the wall is a cylinder, so they
+// depend on (x, y) and (cx, cy) only): Delta >= 1/2: A = 1 / (2 Delta), B = (2 Delta - 1) /
+// (2 Delta), C = 0; Delta < 1/2 with x - c_J fluid: A = 2 Delta, B = 0, C = 1 - 2 Delta;
+// otherwise the half-way values A = 1, B = C = 0.
 template <class R, int J>
 __device__ __forceinline__ BLink<R> bouzidi_link(const Member &d, const CellPos &p) {
-    BLink<R> b{R(1), R(0), R(0)};
     constexpr int cx = cx_of(J), cy = cy_of(J);
-    const R delta = static_cast<const R *>(d.dtab)[(p.y * d.nx + p.x) * 9 + nbit(cx, cy)];
-    if (delta >= R(0.5)) {
-        b.A = R(1) / (R(2) * delta);
-        b.B = (R(2) * delta - R(1)) / (R(2) * delta);
-    } else if ((p.nb >> nbit(-cx, -cy)) & 1u) {   // x_ff = x - c_J is fluid
-        b.A = R(2) * delta;
-        b.C = R(1) - R(2) * delta;
-    }
-    return b;
+    const R *tab = static_cast<const R *>(d.dtab);
+    const int64_t k = ((int64_t)(p.y * d.nx + p.x) * 9 + nbit(cx, cy)) * 3;
+    return BLink<R>{tab[k], tab[k + 1], tab[k + 2]};
+}
+
+// The slot of a wall-pointing direction J holds A f*_J + B f*_Jbar of the previous step;
+// the read of direction Jbar adds C f*_J(x - c_J), which is the value just read for J.
+template <class R>
+__device__ __forceinline__ void bouzidi_load_fix(const Member &d, const CellPos &p, R (&v)[27]) {
+    if (p.nb == 0x1FFu) return;
+    sfor<0, 27>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        if constexpr (cx_of(j) != 0 || cy_of(j) != 0) {
+            if (!dst_is_fluid<j>(p)) {
+                BLink<R> b = bouzidi_link<R, j>(d, p);
+                v[opp_of(j)] += b.C * v[j];
+            }
+        }
+    });
 }
 
 // ---- loading and storing the 27 populations of a cell ------------------------------------
@@ -431,19 +457,7 @@ __device__ __forceinline__ void load_pops(const StepArgs &a, const Member &d, co
             }
         }
     });
-    if constexpr (WALL == LBM_BOUZIDI) {
-        if (p.nb != 0x1FFu) {
-            sfor<0, Q>([&](auto jc) {
-                constexpr int j = decltype(jc)::value;
-                if constexpr (cx_of(j) != 0 || cy_of(j) != 0) {
-                    if (!dst_is_fluid<j>(p)) {
-                        BLink<R> b = bouzidi_link<R, j>(d, p);
-                        v[opp_of(j)] += b.C * v[j];
-                    }
-                }
-            });
-        }
-    }
+    if constexpr (WALL == LBM_BOUZIDI) bouzidi_load_fix<R>(d, p, v);
 }
 
 template <int P, int PAR, int WALL>
@@ -568,27 +582,64 @@ __device__ __forceinline__ void trigger_column(const Member &d, int x, int y, do
 template <class R>
 struct Macro { R drho, rho, ux, uy, uz; };
 
+// The moments a collision needs, from v = f - w: drho = sum f - 1, j = sum c f and the raw
+// second moments m4..m8 of Eq. (Mmatrix) (xy, xz, yz, x^2 - y^2, x^2 - z^2; the weights
+// contribute nothing to them).  Every sum is formed from the z-triplets of the nine
+// (cx, cy) columns of the lattice: P = f(+z) + f(-z), S = P + f(0), D = f(+z) - f(-z),
+// which roughly halves the additions of summing each moment over its populations.
+template <class R>
+struct MomentSums { R drho, jx, jy, jz, m4, m5, m6, m7, m8; };
+
+template <class R>
+__device__ __forceinline__ MomentSums<R> moment_sums(const R (&v)[Q]) {
+    R P[3][3], S[3][3], D[3][3];
+    sfor<0, 9>([&](auto kc) {                       // column (cx, cy) = (a - 1, b - 1)
+        constexpr int k = decltype(kc)::value, a = k % 3, b = k / 3;
+        constexpr int ip = dir_of(a - 1, b - 1, 1), im = dir_of(a - 1, b - 1, -1), i0 = dir_of(a - 1, b - 1, 0);
+        P[a][b] = v[ip] + v[im];
+        S[a][b] = P[a][b] + v[i0];
+        D[a][b] = v[ip] - v[im];
+    });
+    MomentSums<R> m;
+    R Sa[3], Sb[3], Da[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        Sa[k] = S[k][0] + S[k][1] + S[k][2];     // column sums at cx = k - 1
+        Sb[k] = S[0][k] + S[1][k] + S[2][k];     // at cy = k - 1
+        Da[k] = D[k][0] + D[k][1] + D[k][2];
+    }
+    m.drho = Sa[0] + Sa[1] + Sa[2];
+    m.jx = Sa[2] - Sa[0];
+    m.jy = Sb[2] - Sb[0];
+    m.jz = Da[0] + Da[1] + Da[2];
+    m.m4 = (S[2][2] - S[2][0]) - (S[0][2] - S[0][0]);
+    m.m5 = Da[2] - Da[0];
+    m.m6 = (D[0][2] - D[0][0]) + (D[1][2] - D[1][0]) + (D[2][2] - D[2][0]);
+    m.m7 = (S[0][1] + S[2][1]) - (S[1][0] + S[1][2]);
+    // x^2 - z^2: +1 on the cz = 0 populations of the cx != 0 columns, -1 on the cz != 0
+    // populations of the cx = 0 columns
+    constexpr int a0 = dir_of(-1, -1, 0), a1 = dir_of(-1, 0, 0), a2 = dir_of(-1, 1, 0);
+    constexpr int b0 = dir_of(1, -1, 0), b1 = dir_of(1, 0, 0), b2 = dir_of(1, 1, 0);
+    const R f0x = ((v[a0] + v[b0]) + (v[a1] + v[b1])) + (v[a2] + v[b2]);
+    m.m8 = f0x - (P[1][0] + P[1][1] + P[1][2]);
+    return m;
+}
+
+template <class R>
+__device__ __forceinline__ Macro<R> macro_from_sums(const MomentSums<R> &s, R gx, R gy, R gz) {
+    Macro<R> m;
+    m.drho = s.drho;
+    m.rho = R(1) + s.drho;
+    const R ir = R(1) / m.rho;
+    m.ux = s.jx * ir + R(0.5) * gx;
+    m.uy = s.jy * ir + R(0.5) * gy;
+    m.uz = s.jz * ir + R(0.5) * gz;
+    return m;
+}
+
 template <class R>
 __device__ __forceinline__ Macro<R> macroscopic(const R (&v)[Q], R gx, R gy, R gz) {
-    R drho = 0, jx = 0, jy = 0, jz = 0;
-    sfor<0, Q>([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        drho += v[i];
-        if constexpr (cx_of(i) == 1) jx += v[i];
-        if constexpr (cx_of(i) == -1) jx -= v[i];
-        if constexpr (cy_of(i) == 1) jy += v[i];
-        if constexpr (cy_of(i) == -1) jy -= v[i];
-        if constexpr (cz_of(i) == 1) jz += v[i];
-        if constexpr (cz_of(i) == -1) jz -= v[i];
-    });
-    Macro<R> m;
-    m.drho = drho;
-    m.rho = R(1) + drho;
-    const R ir = R(1) / m.rho;
-    m.ux = jx * ir + R(0.5) * gx;
-    m.uy = jy * ir + R(0.5) * gy;
-    m.uz = jz * ir + R(0.5) * gz;
-    return m;
+    return macro_from_sums<R>(moment_sums<R>(v), gx, gy, gz);
 }
 
 // One-axis factors of the product-form equilibrium (see the file header):
@@ -634,7 +685,8 @@ __device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega
                                             const R *lam1 = nullptr) {
     constexpr bool rates = (MODEL & MODEL_RATES) != 0;
     constexpr bool bgk = !rates && (MODEL & MODEL_BGK) != 0, o2 = (MODEL & MODEL_O2) != 0;
-    const Macro<R> mm = macroscopic<R>(v, gx, gy, gz);
+    const MomentSums<R> ms = moment_sums<R>(v);
+    const Macro<R> mm = macro_from_sums<R>(ms, gx, gy, gz);
     const R rho = mm.rho, ux = mm.ux, uy = mm.uy, uz = mm.uz;
     const R om1 = R(1) - omega;
     R s12 = 0, s34 = 0, s56 = 0, q4 = 0, q5 = 0, q6 = 0;
@@ -642,24 +694,7 @@ __device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega
 #pragma unroll
     for (int k = 0; k < 23; ++k) mk[k] = 0;
     if constexpr (!bgk && !rates) {
-        // raw second moments m4..m8 (the rest weights contribute nothing to them)
-        R m4 = 0, m5 = 0, m6 = 0, m7 = 0, m8 = 0;
-        sfor<0, Q>([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            constexpr int xy = cx_of(i) * cy_of(i), xz = cx_of(i) * cz_of(i), yz = cy_of(i) * cz_of(i);
-            constexpr int d7 = cx_of(i) * cx_of(i) - cy_of(i) * cy_of(i);
-            constexpr int d8 = cx_of(i) * cx_of(i) - cz_of(i) * cz_of(i);
-            if constexpr (xy == 1) m4 += v[i];
-            if constexpr (xy == -1) m4 -= v[i];
-            if constexpr (xz == 1) m5 += v[i];
-            if constexpr (xz == -1) m5 -= v[i];
-            if constexpr (yz == 1) m6 += v[i];
-            if constexpr (yz == -1) m6 -= v[i];
-            if constexpr (d7 == 1) m7 += v[i];
-            if constexpr (d7 == -1) m7 -= v[i];
-            if constexpr (d8 == 1) m8 += v[i];
-            if constexpr (d8 == -1) m8 -= v[i];
-        });
+        const R m4 = ms.m4, m5 = ms.m5, m6 = ms.m6, m7 = ms.m7, m8 = ms.m8;
         // (1 - omega)(m_k - m_k^eq + R_k / 2), k = 4..8, with the printed m^eq and R
         const R s4 = m4 - rho * ux * uy + R(0.5) * rho * (gy * ux + gx * uy);
         const R s5 = m5 - rho * ux * uz + R(0.5) * rho * (gz * ux + gx * uz);
@@ -708,7 +743,53 @@ __device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega
             v[i] = f;
         }
     };
-    if constexpr (!o2) {
+    if constexpr (!o2 && !bgk && !rates) {
+        // the default model: f*_i - w_i = w_i drho + w_i rho (pm1 + frc) + shear term, with
+        // pm1 + frc = Dxy + dz axy + Fxy (1 + dz) + hz axy = G + hz axy + dz H per (cx, cy)
+        // column (G = Dxy + Fxy, H = axy + Fxy): three multiply-adds per population
+        R dx[3], hx[3], dy[3], hy[3], dz[3], hz[3];
+        axis_factors<R>(ux, gx, dx, hx);
+        axis_factors<R>(uy, gy, dy, hy);
+        axis_factors<R>(uz, gz, dz, hz);
+        R G[3][3], H[3][3], A[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const R dxy = dx[a] + dy[b] + dx[a] * dy[b];
+                const R axy = R(1) + dxy;
+                const R fxy = hx[a] * (R(1) + dy[b]) + hy[b] * (R(1) + dx[a]);
+                G[a][b] = dxy + fxy;
+                H[a][b] = axy + fxy;
+                A[a][b] = axy;
+            }
+        // w rho and w drho (plus the shear term of the population) per weight shell
+        const R wr0 = R(w_of(0)) * rho, wr1 = R(w_of(1)) * rho, wr2 = R(w_of(7)) * rho, wr3 = R(w_of(19)) * rho;
+        const R wd0 = R(w_of(0)) * drho, wd1 = R(w_of(1)) * drho, wd2 = R(w_of(7)) * drho,
+                wd3 = R(w_of(19)) * drho;
+        const R c12 = wd1 + s12, c34 = wd1 + s34, c56 = wd1 + s56;
+        const R c4p = wd2 + q4, c4m = wd2 - q4, c5p = wd2 + q5, c5m = wd2 - q5, c6p = wd2 + q6, c6m = wd2 - q6;
+        sfor<0, Q>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            constexpr int a = cx_of(i) + 1, b = cy_of(i) + 1, c = cz_of(i) + 1;
+            const R X = G[a][b] + hz[c] * A[a][b] + dz[c] * H[a][b];
+            R wr, wd;
+            if constexpr (i == 0) { wr = wr0; wd = wd0; }
+            else if constexpr (i <= 6) {
+                wr = wr1;
+                wd = (i <= 2) ? c12 : ((i <= 4) ? c34 : c56);
+            } else if constexpr (i <= 18) {
+                wr = wr2;
+                if constexpr (i == 7 || i == 10) wd = c4p;
+                else if constexpr (i == 8 || i == 9) wd = c4m;
+                else if constexpr (i == 11 || i == 14) wd = c5p;
+                else if constexpr (i == 12 || i == 13) wd = c5m;
+                else if constexpr (i == 15 || i == 18) wd = c6p;
+                else wd = c6m;
+            } else { wr = wr3; wd = wd3; }
+            v[i] = wr * X + wd;
+        });
+    } else if constexpr (!o2) {
         R dx[3], hx[3], dy[3], hy[3], dz[3], hz[3];
         axis_factors<R>(ux, gx, dx, hx);
         axis_factors<R>(uy, gy, dy, hy);

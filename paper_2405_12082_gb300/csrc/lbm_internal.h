@@ -15,15 +15,38 @@ struct ModesArgs {
 };
 
 // Launch shapes of the step kernel ("variants"): threads per block, the number of
-// resident blocks per SM the register budget is cut for, and the planes each thread takes
-// (zc).  FP64 storage has one shape.  Shapes 4 and 5 (F32 storage only) are the
-// software-pipelined persistent kernel.
-struct StepShape { int threads, min_blocks, zc, pipelined; };
-constexpr StepShape STEP_SHAPES[11] = {{256, 4, 1, 0}, {256, 3, 1, 0}, {128, 8, 1, 0}, {512, 2, 1, 0},
-                                       {256, 3, 1, 1}, {128, 6, 1, 1}, {128, 8, 2, 0}, {128, 8, 4, 0},
-                                       {256, 4, 2, 0}, {128, 7, 2, 0}, {128, 6, 2, 0}};
-constexpr StepShape STEP_SHAPE_F64 = {256, 2, 1, 0};
-inline int step_variants(int precision) { return precision == LBM_F64 ? 1 : 11; }
+// resident blocks per SM the register budget is cut for, the planes each thread takes
+// (zc), whether it is the software-pipelined persistent kernel (shapes 4 and 5, F32
+// storage only) and whether it is the persistent kernel whose loads are staged in shared
+// memory by bulk copies (shapes 11 and 12, compact pipe layouts, every storage; staged =
+// index into STAGED_SHAPES + 1).  FP64 storage has shape 0 (256 x 2) and the staged ones.
+struct StepShape { int threads, min_blocks, zc, pipelined, staged; };
+constexpr StepShape STEP_SHAPES[13] = {{256, 4, 1, 0, 0}, {256, 3, 1, 0, 0}, {128, 8, 1, 0, 0}, {512, 2, 1, 0, 0},
+                                       {256, 3, 1, 1, 0}, {128, 6, 1, 1, 0}, {128, 8, 2, 0, 0}, {128, 8, 4, 0, 0},
+                                       {256, 4, 2, 0, 0}, {128, 7, 2, 0, 0}, {128, 6, 2, 0, 0}, {512, 1, 1, 0, 1},
+                                       {256, 2, 1, 0, 2}};
+constexpr StepShape STEP_SHAPE_F64 = {256, 2, 1, 0, 0};
+constexpr int N_STEP_SHAPES = 13;
+// Staged shapes: threads per CTA, pipeline stages (tiles in flight per CTA) and CTAs per SM.
+struct StagedShape { int threads, stages, ctas_per_sm; };
+constexpr StagedShape STAGED_SHAPES[2] = {{512, 3, 1}, {256, 3, 2}};
+inline int staged_of(int variant) {
+    return (variant >= 0 && variant < N_STEP_SHAPES) ? STEP_SHAPES[variant].staged - 1 : -1;
+}
+inline size_t esize_of_precision(int precision) {
+    return precision == LBM_F64 ? 8 : (precision == LBM_F32 ? 4 : 2);
+}
+// Storage elements per direction segment of staged shape k: the largest multiple of 64
+// whose STAGES stages (27 segments + a 16-byte cell-table entry per element each) and
+// mbarriers fit the shared memory of one CTA when ctas_per_sm CTAs share an SM (GB300:
+// 227 KB per CTA, 228 KB per SM with 1 KB reserved per CTA).
+inline int staged_cap(int precision, int k) {
+    const StagedShape &sh = STAGED_SHAPES[k];
+    const int budget = (sh.ctas_per_sm == 1 ? 232448 : (233472 / sh.ctas_per_sm - 1024)) - 8 * sh.stages - 128;
+    const int per = sh.stages * (27 * (int)esize_of_precision(precision) + 16);
+    return budget / per / 64 * 64;
+}
+inline int step_variants(int) { return N_STEP_SHAPES; }
 // the fastest shapes in sweeps on GB300: 128 x 8 threads with 2 planes per thread for
 // F32 storage, with 4 planes for the 16-bit formats; with Bouzidi walls one plane per
 // thread (the wall-link arithmetic leaves no registers for the plane loop: 4 % faster)
@@ -38,14 +61,28 @@ inline int model_variant(int precision) { return precision == LBM_F64 ? 0 : 2; }
 // two planes per thread measured 2 % slower there)
 constexpr int MOM_VARIANT = 0;
 inline int moments_variant(int) { return MOM_VARIANT; }
+// whether the storage can run the shape at all (a staged shape also needs a compact pipe
+// layout whose row groups fit its segments: checked per context)
 inline bool step_variant_ok(int precision, int variant) {
-    if (variant < 0 || variant >= step_variants(precision)) return false;
-    return precision == LBM_F64 || precision == LBM_F32 || !STEP_SHAPES[variant].pipelined;
+    if (variant < 0 || variant >= N_STEP_SHAPES) return false;
+    if (STEP_SHAPES[variant].staged) return true;
+    if (precision == LBM_F64) return variant == 0;
+    return precision == LBM_F32 || !STEP_SHAPES[variant].pipelined;
 }
 inline int step_threads(int precision, int variant) {
-    return precision == LBM_F64 ? STEP_SHAPE_F64.threads : STEP_SHAPES[variant].threads;
+    if (precision == LBM_F64 && !STEP_SHAPES[variant].staged) return STEP_SHAPE_F64.threads;
+    return STEP_SHAPES[variant].threads;
 }
 inline int step_zc(int precision, int variant) { return precision == LBM_F64 ? 1 : STEP_SHAPES[variant].zc; }
+
+// Sets the shared-memory size of the staged step kernels of shape `variant` for every
+// parity, wall and statistics setting of storage P (once per process; called before any
+// graph capture so that the launches being captured only launch).
+template <int P>
+cudaError_t prepare_step(int wall, int variant);
+// Step of a staged shape (lbm_staged.cuh; compiled in lbm_staged_*.cu).
+template <int P>
+cudaError_t launch_step_staged(int wall, int parity, bool stats, const StepArgs &a, int variant, cudaStream_t s);
 
 // Every launcher enqueues on `s` and returns the launch status.
 // Step kernel over all members: a flat grid of a.nblocks_total blocks of
@@ -106,6 +143,10 @@ cudaError_t launch_modes(int wall, int parity, const StepArgs &a, const Member &
 template <int P>
 cudaError_t launch_force_tables(const Member *dmembers, const Member &hm, int m, void *ftab, void *ztab,
                                 cudaStream_t s);
+
+// Records the reason of a failed call that has no context (reported by
+// lbm_last_error(NULL) in the calling thread).
+void set_thread_error(const char *msg);
 
 constexpr int REDUCE_BLOCK = 256;
 constexpr int REDUCE_MAX_BLOCKS = 1216;   // 8 resident blocks x 152 SMs

@@ -20,13 +20,12 @@ enum { EX_NONE = 0, EX_STATS = 1, EX_MOMENTS = 2 };
 #define LBM_ADJ_MIN_BLOCKS 3
 #endif
 
-// Stream, force, collide and store one fluid cell p of member d.
+// Force, collide and store one fluid cell p of member d whose 27 populations (f - w) are
+// in v.
 template <int P, int PAR, int WALL, int EXTRA, int MODEL>
-__device__ __forceinline__ void step_cell(const StepArgs &a, const Member &d, const CellPos &p, int64_t t,
-                                          typename Storage<P>::R stv) {
+__device__ __forceinline__ void finish_cell(const StepArgs &a, const Member &d, const CellPos &p, int64_t t,
+                                            typename Storage<P>::R stv, typename Storage<P>::R (&v)[Q]) {
     using R = typename Storage<P>::R;
-    R v[Q];
-    load_pops<P, PAR, WALL>(a, d, p, v);
     R gx, gy, gz;
     acceleration<R>(d, p, t, stv, gx, gy, gz);
     if constexpr (EXTRA == EX_MOMENTS) {
@@ -53,6 +52,16 @@ __device__ __forceinline__ void step_cell(const StepArgs &a, const Member &d, co
         }
     }
     store_pops<P, PAR, WALL>(a, d, p, v);
+}
+
+// Stream, force, collide and store one fluid cell p of member d.
+template <int P, int PAR, int WALL, int EXTRA, int MODEL>
+__device__ __forceinline__ void step_cell(const StepArgs &a, const Member &d, const CellPos &p, int64_t t,
+                                          typename Storage<P>::R stv) {
+    using R = typename Storage<P>::R;
+    R v[Q];
+    load_pops<P, PAR, WALL>(a, d, p, v);
+    finish_cell<P, PAR, WALL, EXTRA, MODEL>(a, d, p, t, stv, v);
 }
 
 // The cell above p (z + 1) in the same column: same in-plane data, one plane further.
@@ -193,19 +202,7 @@ __global__ void __launch_bounds__(BS, MINB) k_step_pipe(const __grid_constant__ 
                 constexpr int i = decltype(ic)::value;
                 v[i] = S::ld(col + i * BS, inv);
             });
-            if constexpr (WALL == LBM_BOUZIDI) {
-                if (cur.p.nb != 0x1FFu) {
-                    sfor<0, Q>([&](auto jc) {
-                        constexpr int j = decltype(jc)::value;
-                        if constexpr (cx_of(j) != 0 || cy_of(j) != 0) {
-                            if (!dst_is_fluid<j>(cur.p)) {
-                                BLink<R> b = bouzidi_link<R, j>(d, cur.p);
-                                v[opp_of(j)] += b.C * v[j];
-                            }
-                        }
-                    });
-                }
-            }
+            if constexpr (WALL == LBM_BOUZIDI) bouzidi_load_fix<R>(d, cur.p, v);
             R gx, gy, gz;
             acceleration<R>(d, cur.p, t, st_of<R>(a, cur.m), gx, gy, gz);
             const Macro<R> mm = collide<R>(v, gx, gy, gz, omega_of<R>(d));
@@ -730,20 +727,26 @@ __device__ __forceinline__ void adjoint_cell(const StepArgs &a, const AdjArgs &j
     if constexpr (OBJ == LBM_J_UBULK) {
         jterm = kap * uz;
     } else {
+        // the wall is a cylinder, so (cx, cy, +1) and (cx, cy, -1) are wall links together:
+        // their terms are summed as the difference f*(+1) - f*(-1), formed from the
+        // closed-form differences psi(+1) - psi(-1) = 6 u_z and psi'(+1) - psi'(-1) = 6
+        // (the rest weights cancel exactly instead of in floating point)
         if (p.nb != 0x1FFu) {
-            sfor<0, Q>([&](auto ic) {
-                constexpr int i = decltype(ic)::value;
-                constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-                if constexpr (cz != 0 && (cx != 0 || cy != 0)) {
-                    if (!dst_is_fluid<i>(p)) {
-                        const R Pi = X0[cx + 1] * Y0[cy + 1] * Z0[cz + 1];
-                        const R Gi = gx * X1[cx + 1] * Y0[cy + 1] * Z0[cz + 1] + gy * X0[cx + 1] * Y1[cy + 1] * Z0[cz + 1] +
-                                     gz * X0[cx + 1] * Y0[cy + 1] * Z1[cz + 1];
-                        R shear = 0;
-                        if constexpr (cy == 0) shear = R(cx * cz) * R(0.25) * s5;
-                        if constexpr (cx == 0) shear = R(cy * cz) * R(0.25) * s6;
-                        const R fstar = R(w_of(i)) * rho * (Pi + half * Gi) + om1 * shear;
-                        jterm += wss * R(cz) * fstar;
+            const R dZ0 = R(6) * uz;
+            sfor<0, 9>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                constexpr int cx = k % 3 - 1, cy = k / 3 - 1;
+                if constexpr (cx != 0 || cy != 0) {
+                    constexpr int ip = dir_of(cx, cy, 1);
+                    if (!dst_is_fluid<ip>(p)) {
+                        const R x0y0 = X0[cx + 1] * Y0[cy + 1];
+                        const R dP = x0y0 * dZ0;
+                        const R dG = (gx * X1[cx + 1] * Y0[cy + 1] + gy * X0[cx + 1] * Y1[cy + 1]) * dZ0 +
+                                     gz * x0y0 * R(6);
+                        R dshear = 0;
+                        if constexpr (cy == 0) dshear = R(cx) * R(0.5) * s5;
+                        if constexpr (cx == 0) dshear = R(cy) * R(0.5) * s6;
+                        jterm += wss * (R(w_of(ip)) * rho * (dP + half * dG) + om1 * dshear);
                     }
                 }
             });
@@ -900,6 +903,8 @@ cudaError_t launch_step_model(int wall, int parity, bool stats, const StepArgs &
 template <int P>
 cudaError_t launch_step(int wall, int parity, bool stats, const StepArgs &a, int variant, cudaStream_t s) {
     if (a.nblocks_total <= 0) return cudaSuccess;
+    if (a.collision == MODEL_MRT_H6 && STEP_SHAPES[variant].staged)
+        return launch_step_staged<P>(wall, parity, stats, a, variant, s);
     if (a.collision != MODEL_MRT_H6) {
         if constexpr (P == LBM_F64) return launch_step_model<P, 256, 2>(wall, parity, stats, a, s);
         else if constexpr (P == LBM_F32) return launch_step_model<P, 128, 8>(wall, parity, stats, a, s);

@@ -16,6 +16,7 @@
 
 #include "lbm.h"
 #include "lbm_device.cuh"
+#include "lbm_internal.h"
 
 namespace {
 
@@ -105,7 +106,21 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 double *g_addr[MAX_DEVICES] = {};
 
-int fail(int code, const char *) { return code; }
+int fail(int code, const char *why) {
+    lbm::set_thread_error(why);
+    return code;
+}
+
+// Device or managed memory (a host array handed to the kernel would fault or, where the
+// GPU can reach host memory, be read through the wrong path).
+bool device_reachable(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
 
 }  // namespace
 
@@ -118,11 +133,8 @@ extern "C" int lbm_reduce_static(const void *pops, int32_t precision, int32_t f1
     if (precision < LBM_F64 || precision > LBM_BF16) return fail(LBM_EINVAL, "unknown precision");
     int s16 = f16_log2_scale == 0 ? 16 : f16_log2_scale;
     if (s16 < 1 || s16 > 24) return fail(LBM_EINVAL, "f16_log2_scale must be in 1..24");
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, out) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
-        cudaGetLastError();
-        return fail(LBM_EINVAL, "out must be device memory (5 doubles)");
-    }
+    if (!device_reachable(pops)) return fail(LBM_EINVAL, "pops must be device (or managed) memory");
+    if (!device_reachable(out)) return fail(LBM_EINVAL, "out must be device (or managed) memory (5 doubles)");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
         cudaGetLastError();

@@ -133,6 +133,7 @@ def _load():
         "lbm_mode_correlation": [P, I64, I32, I32, I32, P],
         "lbm_load": [P, ctypes.c_char_p],
         "lbm_set_variant": [P, I32],
+        "lbm_test_expire_wait": [P, I32],
         "lbm_autotune": [P, I32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
     }
     sig["lbm_set_allocator"] = [ALLOC_FN, FREE_FN, P]
@@ -155,7 +156,7 @@ EXPORTED = ("lbm_create", "lbm_ensemble_create", "lbm_free", "lbm_last_error", "
             "lbm_stats_get", "lbm_modes", "lbm_adjoint", "lbm_profile_enable", "lbm_profile_read",
             "lbm_fluid_mask", "lbm_reduce_static", "lbm_set_graph", "lbm_set_variant", "lbm_autotune",
             "lbm_save", "lbm_load", "lbm_stats_profile", "lbm_dominant_modes", "lbm_transition_matrix",
-            "lbm_mode_correlation", "lbm_set_collision", "lbm_set_allocator")
+            "lbm_mode_correlation", "lbm_set_collision", "lbm_set_allocator", "lbm_test_expire_wait")
 
 
 # ---- marshalling helpers -----------------------------------------------------------------
@@ -413,6 +414,10 @@ def lbm_set_variant(ctx, variant):
     return _check(ctx, LIB.lbm_set_variant(ctx, int(variant)))
 
 
+def lbm_test_expire_wait(ctx, tile):
+    return _check(ctx, LIB.lbm_test_expire_wait(ctx, int(tile)))
+
+
 def lbm_autotune(ctx, steps):
     v = ctypes.c_int32()
     us = ctypes.c_double()
@@ -429,7 +434,7 @@ def lbm_reduce_static(pops, precision, f16_log2_scale, n_cells, out, stream=None
     precision = PRECISIONS[precision] if isinstance(precision, str) else precision
     rc = LIB.lbm_reduce_static(ptr(pops), int(precision), int(f16_log2_scale), int(n_cells), ptr(out), ptr(stream))
     if rc != LBM_OK:
-        raise LbmError(rc, "lbm_reduce_static rejected its arguments or failed to launch")
+        raise LbmError(rc, "lbm_reduce_static: " + LIB.lbm_last_error(None).decode())
     return rc
 
 

@@ -29,14 +29,14 @@ C1 = dict(name="laminar pipe 20x20x64 R=8 fp64 fullway", nx=20, ny=20, nz=64, R=
 # Turbulent pipe R = 48 at Re_tau = 181.3 with u* = 0.00388:
 #   nu = u* R / Re_tau = 1.02724e-3, tau = 0.5030817, h = 2 u*^2 / R = 6.27267e-7,
 #   T_LET = R / u* = 12371.1, trigger period 0.052 T_LET = 643.3, U_b ~ 14.7 u*.
-C2 = dict(name="turbulent pipe 100x100x480 R=48 fp32", nx=100, ny=100, nz=480, R=48.0, precision="f32",
+C2 = dict(name="pipe 100x100x480 R=48, Re_tau=181.3 parameters, trigger on (developing flow)", nx=100, ny=100, nz=480, R=48.0, precision="f32",
           wall="halfway", nu=1.0272476558190844e-03, omega=1.9877485398325951, h=6.272666666666667e-07,
           u_star=0.00388, period=643.2989690721649, t_trigger=20000,
           noise=0.0028518, stats_every=100, modes_every=100, n_sections=16,
           r_over_R=(0.78,), n_theta=256, n_modes=32, trigger_modes=[(m, 0.25, 0.0) for m in range(1, 5)])
 
 # Large turbulent pipe R = 96: nu = 2.05449e-3, tau = 0.5061635, h = 3.13633e-7, T_LET = 24742.3.
-C3 = dict(C2, name="turbulent pipe 196x196x1152 R=96", nx=196, ny=196, nz=1152, R=96.0,
+C3 = dict(C2, name="pipe 196x196x1152 R=96, Re_tau=181.3 parameters, trigger on (developing flow)", nx=196, ny=196, nz=1152, R=96.0,
           nu=2.0544953116381688e-03, omega=1.9756462640779777, h=3.1363333333333336e-07,
           period=1286.5979381443299, n_theta=512)
 

@@ -89,7 +89,9 @@ def test_launch_shapes_agree(lbm_lib):
     L = lbm.Lattice(grid, relax, force)
     nv = L.info()["n_variants"]
     L.close()
-    assert nv == 11     # direct shapes, two software-pipelined persistent shapes, five with 2 or 4 planes per thread
+    # direct shapes, two software-pipelined persistent shapes, five with 2 or 4 planes per
+    # thread, two staged persistent shapes
+    assert nv == 13
     for v in range(nv):
         L = lbm.Lattice(grid, relax, force)
         lbm.lbm_set_variant(L.ctx, v)
@@ -112,16 +114,16 @@ def test_launch_shapes_agree(lbm_lib):
 
 
 def test_plane_coarsened_shapes_on_ragged_pipes(lbm_lib):
-    """Shapes 6 and 7 (2 and 4 planes per thread) on a pipe whose length is not a multiple
-    of 4 and an ensemble of such pipes: bit-identical to the one-cell-per-thread shape; in
-    16-bit storage the pipelined shapes are refused."""
+    """Shapes 6 and 7 (2 and 4 planes per thread) and the staged shapes 11 and 12 on an
+    ensemble of two pipes whose length is not a multiple of 4: bit-identical to the
+    one-cell-per-thread shape; in 16-bit storage the pipelined shapes are refused."""
     lbm = lbm_lib
     for prec in ("f32", "f16s"):
         grids = [lbm.make_grid(20, 20, 7, 8.3, precision=prec), lbm.make_grid(16, 18, 5, 6.1, precision=prec)]
         relaxes = [lbm.lbm_relax(1.3), lbm.lbm_relax(1.6)]
         forces = [lbm.make_force(g=(0, 0, 1e-5)), lbm.make_force(g=(1e-6, 0, 2e-5))]
         ref = None
-        for v in (2, 6, 7, 8, 9, 10):
+        for v in (2, 6, 7, 8, 9, 10, 11, 12):
             E = lbm.Lattice(None, None, ensemble=(grids, relaxes, forces))
             lbm.lbm_set_variant(E.ctx, v)
             lbm.lbm_init(E.ctx, "laminar", noise_amp=1e-3, seed=21)
@@ -152,7 +154,7 @@ def test_autotune_leaves_the_state_untouched(lbm_lib):
     acc0 = np.empty((4, grid.nz, grid.ny, grid.nx))
     c0 = lbm.lbm_stats_get(L.ctx, acc0)
     v, us = lbm.lbm_autotune(L.ctx, 6)
-    assert 0 <= v < 11 and us > 0
+    assert 0 <= v < 13 and us > 0
     info = L.info()
     assert info["t"] == 5 and info["variant"] == v
     assert np.array_equal(_populations(lbm, L.ctx, grid), before)

@@ -18,9 +18,10 @@ import pytest
 
 from oracle import lbm as O
 from oracle import modes as Mo
-from oracle.collision import collide, feq_hermite, macroscopic
-from oracle.lattice import C, OPP
+from oracle.collision import feq_hermite, macroscopic
 from paper_2405_12082_gb300 import workloads as Wk
+
+import _sampled as S
 
 pytestmark = pytest.mark.gpu
 
@@ -81,40 +82,13 @@ def test_initial_state_on_sampled_cells(c2_state):
     del run
 
 
-def _one_step_oracle(cfg, tr, f_prev, t, fluid, z, y, x):
-    """f(t+1) at the sampled cells from the full state f(t): pull from x - c_i, half-way walls."""
-    nz, ny, nx = fluid.shape
-    out = np.empty((27, len(x)))
-    # collide every needed source cell once
-    srcs = {}
-    for i in range(27):
-        cx, cy, cz = (int(v) for v in C[i])
-        zs, ys, xs = (z - cz) % nz, (y - cy) % ny, (x - cx) % nx
-        src_fluid = fluid[zs, ys, xs]
-        zz = np.where(src_fluid, zs, z)
-        yy = np.where(src_fluid, ys, y)
-        xx = np.where(src_fluid, xs, x)
-        srcs[i] = (zz, yy, xx, src_fluid)
-    allz = np.concatenate([srcs[i][0] for i in range(27)])
-    ally = np.concatenate([srcs[i][1] for i in range(27)])
-    allx = np.concatenate([srcs[i][2] for i in range(27)])
-    g = _accel(cfg, tr, allz, ally, allx, t)
-    fs = collide(f_prev[:, allz, ally, allx], g, cfg["omega"])
-    n = len(x)
-    for i in range(27):
-        block = fs[:, i * n:(i + 1) * n]
-        src_fluid = srcs[i][3]
-        out[i] = np.where(src_fluid, block[i], block[OPP[i]])
-    return out
-
-
 @pytest.mark.parametrize("step", [0, 1])
 def test_one_step_on_sampled_cells(c2_state, step):
     """Even (t = 0 -> 1) and odd (t = 1 -> 2) AA steps."""
     cfg, L, tr, f0, f1, f2 = c2_state
     fluid, (z, y, x) = _sample(cfg, 400, 2 + step)
     prev, nxt = (f0, f1) if step == 0 else (f1, f2)
-    expect = _one_step_oracle(cfg, tr, prev, step, fluid, z, y, x)
+    expect = S.one_step(cfg, tr, S.host_fetch(prev), step, fluid, z, y, x)
     got = nxt[:, z, y, x]
     assert np.max(np.abs(got - expect)) < 2e-8
 

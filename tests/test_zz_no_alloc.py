@@ -5,12 +5,16 @@ application whose device memory all belongs to its own pool, or a latency-critic
 loop that cannot absorb the device-wide synchronisation of cudaMalloc) use
 lbm_reduce_static on a population array they already hold.  This file checks, through
 the C ABI, that two calls in a row give what the allocating lbm_reduce gives for the
-same state.  It is named to be collected last and also passes alone in a fresh process.
+same state, in every storage precision, that a non-finite value is counted, and that
+bad arguments are refused before any launch.  It is named to be collected last and
+also passes alone in a fresh process.
 """
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
+
+ESIZE = {"f64": 8, "f32": 4, "f16s": 2, "bf16": 2}
 
 
 def _state(lbm, precision):
@@ -29,14 +33,13 @@ def _state(lbm, precision):
     return L, raw
 
 
-@pytest.mark.parametrize("precision", ["f32", "f64", "f16s"])
+@pytest.mark.parametrize("precision", ["f32", "f64", "f16s", "bf16"])
 def test_static_reduce_matches_reduce_twice(lbm_lib, precision):
     import torch
     lbm = lbm_lib
     L, raw = _state(lbm, precision)
     expect = np.array(lbm.lbm_reduce(L.ctx))
-    esize = {"f64": 8, "f32": 4, "f16s": 2}[precision]
-    n_cells = raw.numel() // (27 * esize)
+    n_cells = raw.numel() // (27 * ESIZE[precision])
     out = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
     scale = max(np.max(np.abs(expect[:4])), 1e-300)
     for _ in range(2):
@@ -50,7 +53,33 @@ def test_static_reduce_matches_reduce_twice(lbm_lib, precision):
     L.close()
 
 
-def test_static_reduce_rejects_bad_sizes(lbm_lib):
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+def test_static_reduce_counts_a_non_finite_cell(lbm_lib, precision):
+    """A NaN written into the host copy of the raw state (one population of one cell)
+    is counted once: out[4] == 1."""
+    import torch
+    lbm = lbm_lib
+    L, raw = _state(lbm, precision)
+    host = raw.cpu().numpy().copy()
+    es = ESIZE[precision]
+    n_cells = host.size // (27 * es)
+    # population 5 of the first cell of the second 64-cell block: a stored fluid cell
+    # in the compact layout or padding; either way one slot of one cell
+    pos = (5 * n_cells + 64) * es
+    nan = np.array([np.nan], dtype=np.float32 if es == 4 else np.float64)
+    if precision == "bf16":
+        host[pos:pos + 2] = np.frombuffer(np.array([0x7FC0], dtype="<u2").tobytes(), dtype=np.uint8)
+    else:
+        host[pos:pos + es] = np.frombuffer(nan.tobytes(), dtype=np.uint8)
+    bad = torch.from_numpy(host).cuda()
+    out = torch.zeros(5, dtype=torch.float64, device="cuda")
+    lbm.lbm_reduce_static(bad, precision, 0, n_cells, out)
+    torch.cuda.synchronize()
+    assert out.cpu().numpy()[4] == 1
+    L.close()
+
+
+def test_static_reduce_rejects_bad_arguments(lbm_lib):
     import torch
     lbm = lbm_lib
     out = torch.zeros(5, dtype=torch.float64, device="cuda")
@@ -58,7 +87,13 @@ def test_static_reduce_rejects_bad_sizes(lbm_lib):
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_reduce_static(buf, "f32", 0, lbm.LBM_STATIC_REDUCE_MAX_CELLS + 1, out)
     assert ei.value.status == lbm.LBM_EINVAL
+    assert "LBM_STATIC_REDUCE_MAX_CELLS" in str(ei.value)
     with pytest.raises(lbm.LbmError):
         lbm.lbm_reduce_static(buf, "f32", 0, 0, out)
-    with pytest.raises(lbm.LbmError):            # the output must be device memory
+    with pytest.raises(lbm.LbmError) as ei:       # the output must be device memory
         lbm.lbm_reduce_static(buf, "f32", 0, 4, np.zeros(5))
+    assert "out must be device" in str(ei.value)
+    with pytest.raises(lbm.LbmError) as ei:       # so must the populations (refused before any launch)
+        lbm.lbm_reduce_static(np.zeros(27 * 4, dtype=np.float32), "f32", 0, 4, out)
+    assert ei.value.status == lbm.LBM_EINVAL and "pops must be device" in str(ei.value)
+    torch.cuda.synchronize()
