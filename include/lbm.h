@@ -259,7 +259,7 @@ int lbm_set_graph(lbm_ctx *ctx, int32_t chunk);
  * copies its next cell's 27 populations into shared memory with cp.async while it
  * computes the current one); 6 = 128 x 8 with each thread taking 2 consecutive planes
  * of one in-plane position (the default for F32 storage), 7 = the same with 4 planes
- * (the default for the 16-bit formats; with LBM_BOUZIDI walls the default is 2), 8 = 256 x 4, 9 = 128 x 7 and 10 = 128 x 6 with 2
+ * (the default for the 16-bit formats and for LBM_BOUZIDI walls), 8 = 256 x 4, 9 = 128 x 7 and 10 = 128 x 6 with 2
  * planes; 11 and 12 = the staged persistent kernel (512 threads with 3 tiles in flight,
  * one CTA per SM; 256 threads, 3 tiles, two CTAs per SM): a tile is a group of whole
  * fluid rows of one plane, whose populations the kernel copies into shared memory with

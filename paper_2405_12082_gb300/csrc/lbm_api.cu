@@ -1443,17 +1443,23 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     const size_t nd = (size_t)d.cells;       // dense cells (dJ/dg_z)
     // temporaries: checkpoints, a work copy of the populations, per-step moments of one
     // segment, two adjoint buffers, FP64 accumulators
-    void *ck = nullptr, *work = nullptr, *mom = nullptr, *lam = nullptr;
+    void *ck = nullptr, *work = nullptr, *mom = nullptr, *lam = nullptr, *accseg = nullptr;
     double *acc = nullptr;
     cudaError_t e = dev_alloc(c, &ck, pop_bytes * (size_t)std::max<int64_t>(nseg - 1, 1));
     if (e == cudaSuccess) e = dev_alloc(c, &work, pop_bytes);
-    if (e == cudaSuccess) e = dev_alloc(c, &mom, (size_t)K * 9 * n * es);
+    // two moment buffers when segments are recomputed: the recompute of segment s - 1 fills
+    // one while the backward steps of segment s read the other
+    const size_t mom_seg = (size_t)K * 9 * n * es;
+    if (e == cudaSuccess) e = dev_alloc(c, &mom, mom_seg * (nseg > 1 ? 2 : 1));
     if (e == cudaSuccess) e = dev_alloc(c, &lam, 2 * 27 * n * es);
+    if (e == cudaSuccess) e = dev_alloc(c, &accseg, n * es);
     // adjoint kernel: 256 threads over (plane pair, stored position)
     const int64_t nblk = ((int64_t)d.Ps * ((d.nz + lbm::ADJ_ZC - 1) / lbm::ADJ_ZC) + 255) / 256;
     const int64_t nslot = nblk * 8;                  // one slot per warp
     if (e == cudaSuccess) e = dev_alloc(c, (void **)&acc, (nd + 2 * nslot) * sizeof(double));
-    auto release = [&]() { dev_free(c, ck); dev_free(c, work); dev_free(c, mom); dev_free(c, lam); dev_free(c, acc); };
+    auto release = [&]() {
+        dev_free(c, ck); dev_free(c, work); dev_free(c, mom); dev_free(c, lam); dev_free(c, acc); dev_free(c, accseg);
+    };
     if (e != cudaSuccess) {
         cudaGetLastError();
         release();
@@ -1484,7 +1490,7 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
             c->variant = lbm::moments_variant(c->precision);
             for (int64_t k = 0; k < ns && rc == LBM_OK; ++k) {
                 StepArgs a = make_args(c, c->t);
-                a.moments = (char *)mom + (size_t)k * 9 * n * es;
+                a.moments = (char *)mom + (size_t)(sgm & 1) * mom_seg + (size_t)k * 9 * n * es;
                 rc = dispatch(c, [&](auto P) {
                     return lbm::launch_step_moments<decltype(P)::value>((int)(c->t & 1), a, c->stream);
                 });
@@ -1502,38 +1508,85 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     j.kappa_f = (float)j.kappa;
     j.wss_f = (float)j.wss;
     j.acc = acc;
+    j.acc_seg = accseg;
     j.blockacc = acc + nd;
     j.nblocks = (int32_t)nblk;
     if (rc == LBM_OK) {
         e = cudaMemsetAsync(lam, 0, 2 * 27 * n * es, c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, (nd + 2 * nslot) * sizeof(double), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(accseg, 0, n * es, c->stream);
         if (e != cudaSuccess) rc = cuda_err(c, e, "adjoint buffer clear");
     }
+    // Reverse sweep.  The backward steps of segment s run on the context's stream while the
+    // recompute of segment s - 1 (from its checkpoint, storing its moments into the other
+    // buffer) runs on a second stream: events order every recompute after the last reader
+    // of its buffer (the backward steps of segment s + 1) and every backward segment after
+    // its recompute.  Both kernels are latency-bound, so running them side by side keeps
+    // more of the GPU busy.
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_bwd[2] = {nullptr, nullptr};
+    if (rc == LBM_OK && nseg > 1) {
+        e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaEventCreateWithFlags(&ev_rec[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_bwd[b], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev_start, c->stream);      // checkpoints are written
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_start, 0);
+        if (e != cudaSuccess) rc = cuda_err(c, e, "adjoint streams");
+    }
+    auto recompute = [&](int64_t sgm) -> int {
+        const int64_t ts = t0 + sgm * K, ns = std::min<int64_t>(K, T - sgm * K);
+        cudaError_t ce = cudaMemcpyAsync(work, (char *)ck + sgm * pop_bytes, pop_bytes, cudaMemcpyDeviceToDevice, side);
+        if (ce != cudaSuccess) return cuda_err(c, ce, "checkpoint restore");
+        for (int64_t k = 0; k < ns; ++k) {
+            StepArgs a = make_args(c, ts + k);
+            a.pops = work;
+            a.moments = (char *)mom + (size_t)(sgm & 1) * mom_seg + (size_t)k * 9 * n * es;
+            const int r = dispatch(c, [&](auto P) {
+                return lbm::launch_step_moments<decltype(P)::value>((int)((ts + k) & 1), a, side);
+            });
+            if (r) return r;
+        }
+        ce = cudaEventRecord(ev_rec[sgm & 1], side);
+        return ce == cudaSuccess ? LBM_OK : cuda_err(c, ce, "adjoint event");
+    };
+    if (rc == LBM_OK && nseg > 1) rc = recompute(nseg - 2);
     for (int64_t sgm = nseg - 1; sgm >= 0 && rc == LBM_OK; --sgm) {
         const int64_t ts = t0 + sgm * K, ns = std::min<int64_t>(K, T - sgm * K);
         if (sgm < nseg - 1) {
-            e = cudaMemcpyAsync(work, (char *)ck + sgm * pop_bytes, pop_bytes, cudaMemcpyDeviceToDevice, c->stream);
-            if (e != cudaSuccess) { rc = cuda_err(c, e, "checkpoint restore"); break; }
+            e = cudaStreamWaitEvent(c->stream, ev_rec[sgm & 1], 0);           // its moments are ready
+            if (e != cudaSuccess) { rc = cuda_err(c, e, "adjoint event wait"); break; }
         }
-        // recompute the segment, storing the moments of every step
-        for (int64_t k = 0; k < ns && rc == LBM_OK && sgm < nseg - 1; ++k) {
-            StepArgs a = make_args(c, ts + k);
-            a.pops = work;
-            a.moments = (char *)mom + (size_t)k * 9 * n * es;
-            rc = dispatch(c, [&](auto P) {
-                return lbm::launch_step_moments<decltype(P)::value>((int)((ts + k) & 1), a, c->stream);
-            });
-        }
-        // reverse sweep through the segment
         for (int64_t k = ns - 1; k >= 0 && rc == LBM_OK; --k) {
             const int64_t t = ts + k;
             StepArgs a = make_args(c, t);
             j.lam_next = (char *)lam + (size_t)((t + 1) & 1) * 27 * n * es;
             j.lam = (char *)lam + (size_t)(t & 1) * 27 * n * es;
-            j.moments = (char *)mom + (size_t)k * 9 * n * es;
+            j.moments = (char *)mom + (size_t)(sgm & 1) * mom_seg + (size_t)k * 9 * n * es;
             rc = dispatch(c, [&](auto P) { return lbm::launch_adjoint<decltype(P)::value>(a, j, c->stream); });
         }
+        if (rc == LBM_OK) {
+            const StepArgs a = make_args(c, ts);
+            rc = dispatch(c, [&](auto P) {
+                return lbm::launch_flush_segment<decltype(P)::value>(a, d, j, c->stream);
+            });
+        }
+        if (rc == LBM_OK && sgm >= 2) {
+            // the recompute of segment sgm - 2 reuses this segment's moment buffer
+            e = cudaEventRecord(ev_bwd[sgm & 1], c->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_bwd[sgm & 1], 0);
+            if (e != cudaSuccess) { rc = cuda_err(c, e, "adjoint event"); break; }
+            rc = recompute(sgm - 2);
+        }
     }
+    if (side) {
+        cudaStreamSynchronize(side);
+        cudaStreamDestroy(side);
+    }
+    for (cudaEvent_t ev : {ev_start, ev_rec[0], ev_rec[1], ev_bwd[0], ev_bwd[1]})
+        if (ev) cudaEventDestroy(ev);
     // J and dJ/domega: deterministic sums over cells; dJ/dg_z per cell
     double host[5] = {0, 0, 0, 0, 0};
     if (rc == LBM_OK) {

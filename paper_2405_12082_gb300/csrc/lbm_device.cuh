@@ -146,26 +146,40 @@ constexpr MtInverse make_mt_inverse() {
 constexpr MtInverse kMtInv = make_mt_inverse();
 
 // ---- storage ------------------------------------------------------------------------
+// ld / st convert between the stored value and f - w; ldr / str move the stored value
+// unscaled (the step kernels of the scaled half format work in units of 2^-s, see collide).
 template <int P> struct Storage;
 template <> struct Storage<LBM_F64> {
     using T = double; using R = double;
+    static constexpr bool kScaled = false;
     static __device__ __forceinline__ R ld(const T *p, R) { return *p; }
     static __device__ __forceinline__ void st(T *p, R v, R) { *p = v; }
+    static __device__ __forceinline__ R ldr(const T *p) { return *p; }
+    static __device__ __forceinline__ void str(T *p, R v) { *p = v; }
 };
 template <> struct Storage<LBM_F32> {
     using T = float; using R = float;
+    static constexpr bool kScaled = false;
     static __device__ __forceinline__ R ld(const T *p, R) { return *p; }
     static __device__ __forceinline__ void st(T *p, R v, R) { *p = v; }
+    static __device__ __forceinline__ R ldr(const T *p) { return *p; }
+    static __device__ __forceinline__ void str(T *p, R v) { *p = v; }
 };
 template <> struct Storage<LBM_F16S> {
     using T = __half; using R = float;
+    static constexpr bool kScaled = true;
     static __device__ __forceinline__ R ld(const T *p, R inv_scale) { return __half2float(*p) * inv_scale; }
     static __device__ __forceinline__ void st(T *p, R v, R scale) { *p = __float2half_rn(v * scale); }
+    static __device__ __forceinline__ R ldr(const T *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void str(T *p, R v) { *p = __float2half_rn(v); }
 };
 template <> struct Storage<LBM_BF16> {
     using T = __nv_bfloat16; using R = float;
+    static constexpr bool kScaled = false;
     static __device__ __forceinline__ R ld(const T *p, R) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(T *p, R v, R) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ R ldr(const T *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void str(T *p, R v) { *p = __float2bfloat16_rn(v); }
 };
 
 // ---- per-member description (host fills, device reads) ---------------------------------
@@ -432,7 +446,19 @@ __device__ __forceinline__ void bouzidi_load_fix(const Member &d, const CellPos 
 // across a wall link.  Slot written: PAR 0 -> (ibar, x); PAR 1 -> (i, x + c_i), or (ibar, x)
 // across a wall link.  Wall links choose the address with a select, not a branch.
 // Element indices are 32-bit: the library keeps 27 x stride below 2^32.
-template <int P, int PAR, int WALL>
+// RAW: the values stay in storage units (only the step kernels, see collide).
+template <int P, bool RAW>
+__device__ __forceinline__ typename Storage<P>::R ld_pop(const typename Storage<P>::T *q, typename Storage<P>::R inv) {
+    if constexpr (RAW) return Storage<P>::ldr(q);
+    else return Storage<P>::ld(q, inv);
+}
+template <int P, bool RAW>
+__device__ __forceinline__ void st_pop(typename Storage<P>::T *q, typename Storage<P>::R v, typename Storage<P>::R sc) {
+    if constexpr (RAW) Storage<P>::str(q, v);
+    else Storage<P>::st(q, v, sc);
+}
+
+template <int P, int PAR, int WALL, bool RAW = false>
 __device__ __forceinline__ void load_pops(const StepArgs &a, const Member &d, const CellPos &p,
                                           typename Storage<P>::R (&v)[Q]) {
     using S = Storage<P>;
@@ -446,21 +472,21 @@ __device__ __forceinline__ void load_pops(const StepArgs &a, const Member &d, co
         constexpr int i = decltype(ic)::value;
         constexpr int ib = opp_of(i);
         if constexpr (PAR == 0) {
-            v[i] = S::ld(base + (i * st + lc), inv);
+            v[i] = ld_pop<P, RAW>(base + (i * st + lc), inv);
         } else {
             const uint32_t pull = ib * st + (uint32_t)(p.lc + src_offset<i>(p));
             if constexpr (WALL == LBM_FULLWAY || (cx_of(i) == 0 && cy_of(i) == 0)) {
-                v[i] = S::ld(base + pull, inv);
+                v[i] = ld_pop<P, RAW>(base + pull, inv);
             } else {
                 const uint32_t own = i * st + lc;
-                v[i] = S::ld(base + (src_is_fluid<i>(p) ? pull : own), inv);
+                v[i] = ld_pop<P, RAW>(base + (src_is_fluid<i>(p) ? pull : own), inv);
             }
         }
     });
     if constexpr (WALL == LBM_BOUZIDI) bouzidi_load_fix<R>(d, p, v);
 }
 
-template <int P, int PAR, int WALL>
+template <int P, int PAR, int WALL, bool RAW = false>
 __device__ __forceinline__ void store_pops(const StepArgs &a, const Member &d, const CellPos &p,
                                            typename Storage<P>::R (&v)[Q]) {
     using S = Storage<P>;
@@ -491,14 +517,14 @@ __device__ __forceinline__ void store_pops(const StepArgs &a, const Member &d, c
         constexpr int i = decltype(ic)::value;
         constexpr int ib = opp_of(i);
         if constexpr (PAR == 0) {
-            S::st(base + (ib * st + lc), v[i], sc);
+            st_pop<P, RAW>(base + (ib * st + lc), v[i], sc);
         } else {
             const uint32_t push = i * st + (uint32_t)(p.lc + nb_offset<i>(p));
             if constexpr (WALL == LBM_FULLWAY || (cx_of(i) == 0 && cy_of(i) == 0)) {
-                S::st(base + push, v[i], sc);
+                st_pop<P, RAW>(base + push, v[i], sc);
             } else {
                 const uint32_t own = ib * st + lc;
-                S::st(base + (dst_is_fluid<i>(p) ? push : own), v[i], sc);
+                st_pop<P, RAW>(base + (dst_is_fluid<i>(p) ? push : own), v[i], sc);
             }
         }
     });
@@ -680,12 +706,22 @@ template <int E, class R> __device__ __forceinline__ R cterm(R acc, R x) {
 // for the BGK, N = f - f^eq + F/2.  MODEL_RATES takes a general diagonal Lambda:
 // f* = f^eq + F/2 + (M^T)^{-1} (1 - Lambda) M^T n with n = f - f^eq + F/2, whose moments
 // 0..3 vanish (lam1[k - 4] = 1 - lambda_k).
-template <class R, int MODEL = MODEL_MRT_H6>
+//
+// SCALED (default model only): v holds (f - w) sc on entry and leaves with (f* - w) sc,
+// sc = 1 / inv a power of two (the half format's scale): the moment sums are taken in
+// those units and multiplied by inv once, and sc enters the output constants, which is
+// exact and saves the per-population scaling of loads and stores.
+template <class R, int MODEL = MODEL_MRT_H6, bool SCALED = false>
 __device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega, R *s_out = nullptr,
-                                            const R *lam1 = nullptr) {
+                                            const R *lam1 = nullptr, R inv = R(1), R sc = R(1)) {
     constexpr bool rates = (MODEL & MODEL_RATES) != 0;
     constexpr bool bgk = !rates && (MODEL & MODEL_BGK) != 0, o2 = (MODEL & MODEL_O2) != 0;
-    const MomentSums<R> ms = moment_sums<R>(v);
+    static_assert(!SCALED || MODEL == MODEL_MRT_H6, "scaled units serve the default model only");
+    MomentSums<R> ms = moment_sums<R>(v);
+    if constexpr (SCALED) {
+        ms.drho *= inv; ms.jx *= inv; ms.jy *= inv; ms.jz *= inv;
+        ms.m4 *= inv; ms.m5 *= inv; ms.m6 *= inv; ms.m7 *= inv; ms.m8 *= inv;
+    }
     const Macro<R> mm = macro_from_sums<R>(ms, gx, gy, gz);
     const R rho = mm.rho, ux = mm.ux, uy = mm.uy, uz = mm.uz;
     const R om1 = R(1) - omega;
@@ -704,7 +740,8 @@ __device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega
         if (s_out) {
             s_out[0] = s4; s_out[1] = s5; s_out[2] = s6; s_out[3] = s7; s_out[4] = s8;
         }
-        const R a4 = om1 * s4, a5 = om1 * s5, a6 = om1 * s6, a7 = om1 * s7, a8 = om1 * s8;
+        const R om1s = SCALED ? om1 * sc : om1;
+        const R a4 = om1s * s4, a5 = om1s * s5, a6 = om1s * s6, a7 = om1s * s7, a8 = om1s * s8;
         s12 = (a7 + a8) * R(1.0 / 6.0);
         s34 = a8 * R(1.0 / 6.0) - a7 * R(1.0 / 3.0);
         s56 = a7 * R(1.0 / 6.0) - a8 * R(1.0 / 3.0);
@@ -764,9 +801,12 @@ __device__ __forceinline__ Macro<R> collide(R (&v)[Q], R gx, R gy, R gz, R omega
                 A[a][b] = axy;
             }
         // w rho and w drho (plus the shear term of the population) per weight shell
-        const R wr0 = R(w_of(0)) * rho, wr1 = R(w_of(1)) * rho, wr2 = R(w_of(7)) * rho, wr3 = R(w_of(19)) * rho;
-        const R wd0 = R(w_of(0)) * drho, wd1 = R(w_of(1)) * drho, wd2 = R(w_of(7)) * drho,
-                wd3 = R(w_of(19)) * drho;
+        R w0 = R(w_of(0)), w1 = R(w_of(1)), w2 = R(w_of(7)), w3 = R(w_of(19));
+        if constexpr (SCALED) {
+            w0 *= sc; w1 *= sc; w2 *= sc; w3 *= sc;
+        }
+        const R wr0 = w0 * rho, wr1 = w1 * rho, wr2 = w2 * rho, wr3 = w3 * rho;
+        const R wd0 = w0 * drho, wd1 = w1 * drho, wd2 = w2 * drho, wd3 = w3 * drho;
         const R c12 = wd1 + s12, c34 = wd1 + s34, c56 = wd1 + s56;
         const R c4p = wd2 + q4, c4m = wd2 - q4, c5p = wd2 + q5, c5m = wd2 - q5, c6p = wd2 + q6, c6m = wd2 - q6;
         sfor<0, Q>([&](auto ic) {

@@ -23,13 +23,14 @@ struct ModesArgs {
 struct StepShape { int threads, min_blocks, zc, pipelined, staged; };
 constexpr StepShape STEP_SHAPES[13] = {{256, 4, 1, 0, 0}, {256, 3, 1, 0, 0}, {128, 8, 1, 0, 0}, {512, 2, 1, 0, 0},
                                        {256, 3, 1, 1, 0}, {128, 6, 1, 1, 0}, {128, 8, 2, 0, 0}, {128, 8, 4, 0, 0},
-                                       {256, 4, 2, 0, 0}, {128, 7, 2, 0, 0}, {128, 6, 2, 0, 0}, {512, 1, 1, 0, 1},
-                                       {256, 2, 1, 0, 2}};
+                                       {256, 4, 2, 0, 0}, {128, 7, 2, 0, 0}, {128, 6, 2, 0, 0}, {992, 1, 1, 0, 1},
+                                       {512, 1, 1, 0, 2}};
 constexpr StepShape STEP_SHAPE_F64 = {256, 2, 1, 0, 0};
 constexpr int N_STEP_SHAPES = 13;
-// Staged shapes: threads per CTA, pipeline stages (tiles in flight per CTA) and CTAs per SM.
-struct StagedShape { int threads, stages, ctas_per_sm; };
-constexpr StagedShape STAGED_SHAPES[2] = {{512, 3, 1}, {256, 3, 2}};
+// Staged shapes: threads per CTA (one producer warp, the rest consume), pipeline stages
+// (tiles in flight per CTA), CTAs per SM and consumer groups (tiles worked on at once).
+struct StagedShape { int threads, stages, ctas_per_sm, groups; };
+constexpr StagedShape STAGED_SHAPES[2] = {{992, 3, 1, 2}, {512, 3, 1, 1}};
 inline int staged_of(int variant) {
     return (variant >= 0 && variant < N_STEP_SHAPES) ? STEP_SHAPES[variant].staged - 1 : -1;
 }
@@ -42,17 +43,17 @@ inline size_t esize_of_precision(int precision) {
 // 227 KB per CTA, 228 KB per SM with 1 KB reserved per CTA).
 inline int staged_cap(int precision, int k) {
     const StagedShape &sh = STAGED_SHAPES[k];
-    const int budget = (sh.ctas_per_sm == 1 ? 232448 : (233472 / sh.ctas_per_sm - 1024)) - 8 * sh.stages - 128;
+    const int budget = (sh.ctas_per_sm == 1 ? 232448 : (233472 / sh.ctas_per_sm - 1024)) - 80 * sh.stages - 128;
     const int per = sh.stages * (27 * (int)esize_of_precision(precision) + 16);
     return budget / per / 64 * 64;
 }
 inline int step_variants(int) { return N_STEP_SHAPES; }
 // the fastest shapes in sweeps on GB300: 128 x 8 threads with 2 planes per thread for
-// F32 storage, with 4 planes for the 16-bit formats; with Bouzidi walls one plane per
-// thread (the wall-link arithmetic leaves no registers for the plane loop: 4 % faster)
+// F32 storage, with 4 planes for the 16-bit formats and for Bouzidi walls (with the link
+// coefficients tabulated per wall link, 4 planes per thread beat one by 4 %)
 inline int default_variant(int precision, int wall) {
     if (precision == LBM_F64) return 0;
-    if (wall == LBM_BOUZIDI) return 2;
+    if (wall == LBM_BOUZIDI) return 7;
     return precision == LBM_F32 ? 6 : 7;
 }
 // the shape the ablation collision models are compiled for (one plane per thread)
@@ -103,7 +104,9 @@ struct AdjArgs {
     const void *lam_next;     // lambda_{t+1}, [27][cells] in the compute type
     void *lam;                // lambda_t (written)
     const void *moments;      // [9][cells] of step t: rho, u_x, u_y, u_z, s4..s8
-    double *acc;              // [cells]: dJ/dg_z (accumulated)
+    double *acc;              // [cells]: dJ/dg_z (accumulated, FP64, dense cells)
+    void *acc_seg;            // [stored cells]: dJ/dg_z of the current segment (compute type;
+                              // added into acc and cleared after each segment)
     double *blockacc;         // [2][nblocks * 8]: objective and dJ/domega per warp (accumulated)
     int32_t objective;        // LBM_J_UBULK | LBM_J_WSS
     double kappa;             // UBULK: 1 / (T N_fluid)
@@ -113,6 +116,9 @@ struct AdjArgs {
 };
 template <int P>
 cudaError_t launch_adjoint(const StepArgs &a, const AdjArgs &j, cudaStream_t s);
+// acc[dense cell] += acc_seg[stored cell]; acc_seg = 0 (member 0 of a, compact layout).
+template <int P>
+cudaError_t launch_flush_segment(const StepArgs &a, const Member &hm, const AdjArgs &j, cudaStream_t s);
 // Deterministic column sums of nv <= 5 double arrays [nv][n] into out[5] (device).
 template <int P>
 cudaError_t launch_sum_columns(const double *base, int64_t n, int nv, double *partials, int n_partials_max,

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "lbm_internal.h"
 
@@ -20,8 +21,15 @@ enum { EX_NONE = 0, EX_STATS = 1, EX_MOMENTS = 2 };
 #define LBM_ADJ_MIN_BLOCKS 3
 #endif
 
-// Force, collide and store one fluid cell p of member d whose 27 populations (f - w) are
-// in v.
+// Whether the step's populations travel in storage units (the scaled half format with the
+// default collision: the scale is applied inside collide, see there).
+template <int P, int EXTRA, int MODEL>
+__host__ __device__ constexpr bool raw_units() {
+    return Storage<P>::kScaled && MODEL == MODEL_MRT_H6 && EXTRA != EX_MOMENTS;
+}
+
+// Force, collide and store one fluid cell p of member d whose 27 populations (f - w, or
+// (f - w) 2^s in raw units) are in v.
 template <int P, int PAR, int WALL, int EXTRA, int MODEL>
 __device__ __forceinline__ void finish_cell(const StepArgs &a, const Member &d, const CellPos &p, int64_t t,
                                             typename Storage<P>::R stv, typename Storage<P>::R (&v)[Q]) {
@@ -40,7 +48,9 @@ __device__ __forceinline__ void finish_cell(const StepArgs &a, const Member &d, 
 #pragma unroll
         for (int k = 0; k < 5; ++k) mo[(4 + k) * n] = sk[k];
     } else {
-        const Macro<R> mm = collide<R, MODEL>(v, gx, gy, gz, omega_of<R>(d), nullptr, lam1_of<R>(d));
+        constexpr bool SC = Storage<P>::kScaled && MODEL == MODEL_MRT_H6;
+        const Macro<R> mm = collide<R, MODEL, SC>(v, gx, gy, gz, omega_of<R>(d), nullptr, lam1_of<R>(d),
+                                                  (R)a.f16_inv, (R)a.f16_scale);
         if constexpr (EXTRA == EX_STATS) {
             const double uz = (double)mm.uz;
             double *s = a.stats + d.doff + p.di;
@@ -51,7 +61,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs &a, const Member &d, 
             s[3 * a.dstride] += uz2 * uz2;
         }
     }
-    store_pops<P, PAR, WALL>(a, d, p, v);
+    store_pops<P, PAR, WALL, raw_units<P, EXTRA, MODEL>()>(a, d, p, v);
 }
 
 // Stream, force, collide and store one fluid cell p of member d.
@@ -60,7 +70,7 @@ __device__ __forceinline__ void step_cell(const StepArgs &a, const Member &d, co
                                           typename Storage<P>::R stv) {
     using R = typename Storage<P>::R;
     R v[Q];
-    load_pops<P, PAR, WALL>(a, d, p, v);
+    load_pops<P, PAR, WALL, raw_units<P, EXTRA, MODEL>()>(a, d, p, v);
     finish_cell<P, PAR, WALL, EXTRA, MODEL>(a, d, p, t, stv, v);
 }
 
@@ -755,7 +765,21 @@ __device__ __forceinline__ void adjoint_cell(const StepArgs &a, const AdjArgs &j
     const R gterm = half * rho * K001 + om1 * half * rho * (q5 * ux + q6 * uy - R(2) * q8 * uz) + half * Auz +
                     (OBJ == LBM_J_UBULK ? half * kap : R(0));
     wterm = -(q4 * s4 + q5 * s5 + q6 * s6 + q7 * s7 + q8 * s8);
-    j.acc[p.di] += (double)gterm;
+    static_cast<R *>(j.acc_seg)[p.lc] += gterm;
+}
+
+// End of a segment of the reverse sweep: its dJ/dg_z sums join the FP64 totals (dense cells).
+template <class R>
+__global__ void k_flush_segment(const Member *members, R *acc_seg, double *acc) {
+    const Member &d = members[0];
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.scells) return;
+    const int z = (int)(s / d.Ps), r = (int)(s - (int64_t)z * d.Ps);
+    const int4 ci = d.cellinfo[r];
+    if (ci.x == -1) return;
+    const int y = ci.x & 0xFFFF, x = (int)((uint32_t)ci.x >> 16);
+    acc[((int64_t)z * d.ny + y) * d.nx + x] += (double)acc_seg[s];
+    acc_seg[s] = R(0);
 }
 
 // One thread per ADJ_ZC consecutive planes of one stored position; the objective and
@@ -923,11 +947,11 @@ cudaError_t launch_step(int wall, int parity, bool stats, const StepArgs &a, int
             case 5:
                 if constexpr (P == LBM_F32) return launch_step_pipe<P, 128, 6>(wall, parity, stats, a, s);
                 else return cudaErrorInvalidValue;
-            case 6: return launch_step_shape<P, 128, 8, 2>(wall, parity, stats, a, s);
-            case 7: return launch_step_shape<P, 128, 8, 4>(wall, parity, stats, a, s);
-            case 8: return launch_step_shape<P, 256, 4, 2>(wall, parity, stats, a, s);
-            case 9: return launch_step_shape<P, 128, 7, 2>(wall, parity, stats, a, s);
-            case 10: return launch_step_shape<P, 128, 6, 2>(wall, parity, stats, a, s);
+            case 6: return launch_step_shape<P, STEP_SHAPES[6].threads, STEP_SHAPES[6].min_blocks, STEP_SHAPES[6].zc>(wall, parity, stats, a, s);
+            case 7: return launch_step_shape<P, STEP_SHAPES[7].threads, STEP_SHAPES[7].min_blocks, STEP_SHAPES[7].zc>(wall, parity, stats, a, s);
+            case 8: return launch_step_shape<P, STEP_SHAPES[8].threads, STEP_SHAPES[8].min_blocks, STEP_SHAPES[8].zc>(wall, parity, stats, a, s);
+            case 9: return launch_step_shape<P, STEP_SHAPES[9].threads, STEP_SHAPES[9].min_blocks, STEP_SHAPES[9].zc>(wall, parity, stats, a, s);
+            case 10: return launch_step_shape<P, STEP_SHAPES[10].threads, STEP_SHAPES[10].min_blocks, STEP_SHAPES[10].zc>(wall, parity, stats, a, s);
             default: return launch_step_shape<P, 256, 4>(wall, parity, stats, a, s);
         }
     }
@@ -965,6 +989,17 @@ cudaError_t launch_adjoint(const StepArgs &a, const AdjArgs &j, cudaStream_t s) 
     if constexpr (P == LBM_F64 || P == LBM_F32) {
         if (j.objective == LBM_J_UBULK) k_adjoint<P, LBM_J_UBULK><<<j.nblocks, 256, 0, s>>>(a, j);
         else k_adjoint<P, LBM_J_WSS><<<j.nblocks, 256, 0, s>>>(a, j);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
+template <int P>
+cudaError_t launch_flush_segment(const StepArgs &a, const Member &hm, const AdjArgs &j, cudaStream_t s) {
+    using R = typename Storage<P>::R;
+    if constexpr (P == LBM_F64 || P == LBM_F32) {
+        k_flush_segment<R><<<blocks_for(hm.scells, 256), 256, 0, s>>>(a.members, static_cast<R *>(j.acc_seg), j.acc);
         return cudaGetLastError();
     } else {
         return cudaErrorNotSupported;
@@ -1055,6 +1090,8 @@ cudaError_t launch_modes(int wall, int parity, const StepArgs &a, const Member &
     template cudaError_t launch_step<P>(int, int, bool, const StepArgs &, int, cudaStream_t);           \
     template cudaError_t launch_step_moments<P>(int, const StepArgs &, cudaStream_t);                    \
     template cudaError_t launch_adjoint<P>(const StepArgs &, const AdjArgs &, cudaStream_t);             \
+    template cudaError_t launch_flush_segment<P>(const StepArgs &, const Member &, const AdjArgs &,       \
+                                                 cudaStream_t);                                          \
     template cudaError_t launch_sum_columns<P>(const double *, int64_t, int, double *, int, double *,    \
                                                cudaStream_t);                                            \
     template cudaError_t launch_moments<P>(int, int, const StepArgs &, const Member &, int, void *,     \

@@ -76,8 +76,11 @@ def compare(profiles, ref="f64"):
 
 
 def run(lbm, cfg, spin_steps, window, stats_every=100, nbins=None, dr=2.0, precisions=PRECISIONS,
-        wall="halfway", log=None):
-    """Spin-up, copy and windows; returns the profiles, the comparison and timings."""
+        wall="halfway", log=None, reference="f64", control=False):
+    """Spin-up, copy and windows; returns the profiles, the comparison against `reference`
+    and timings.  control: the reference storage also runs the window that follows its
+    first one ("<reference>:next"); its difference from the first window is the sampling
+    error of a window of this length (the floor of any comparison)."""
     import torch
     nbins = nbins or int(cfg["R"] / dr)
     t0 = time.time()
@@ -99,12 +102,15 @@ def run(lbm, cfg, spin_steps, window, stats_every=100, nbins=None, dr=2.0, preci
         profiles[p], bad[p] = window_profile(lbm, L, window, stats_every, nbins, dr)
         torch.cuda.synchronize()
         timings[p] = time.time() - t1
+        if control and p == reference:
+            key = p + ":next"
+            profiles[key], bad[key] = window_profile(lbm, L, window, stats_every, nbins, dr)
         L.close()
         if log:
             log({"precision": p, "window_s": timings[p], "nonfinite": bad[p]})
     S.close()
-    return {"state": state, "profiles": profiles, "errors": compare(profiles), "window_s": timings,
-            "nonfinite": bad}
+    return {"state": state, "profiles": profiles, "errors": compare(profiles, reference), "window_s": timings,
+            "nonfinite": bad, "reference": reference}
 
 
 def main(argv=None):
@@ -116,17 +122,22 @@ def main(argv=None):
     ap.add_argument("--window", type=int, default=20000, help="compared window in steps")
     ap.add_argument("--stats-every", type=int, default=100)
     ap.add_argument("--wall", default="halfway", choices=["halfway", "bouzidi"])
+    ap.add_argument("--precisions", default=",".join(PRECISIONS))
+    ap.add_argument("--reference", default="f64", choices=list(PRECISIONS))
+    ap.add_argument("--control", action="store_true",
+                    help="also run the reference over the following window (sampling-error floor)")
     ap.add_argument("--out", default="precision_study.npz")
     a = ap.parse_args(argv)
     cfg = dict({"paper": Wk.C_PAPER, "c2": Wk.C2, "c3": Wk.C3}[a.workload])
     spin = int(round(a.spin * cfg["R"] / cfg["u_star"]))
-    res = run(lbm, cfg, spin, a.window, a.stats_every, wall=a.wall,
-              log=lambda d: print(json.dumps(d), file=sys.stderr, flush=True))
-    np.savez(a.out, **{"profile_" + p: v for p, v in res["profiles"].items()})
+    precs = tuple(p for p in a.precisions.split(",") if p)
+    res = run(lbm, cfg, spin, a.window, a.stats_every, wall=a.wall, precisions=precs, reference=a.reference,
+              control=a.control, log=lambda d: print(json.dumps(d), file=sys.stderr, flush=True))
+    np.savez(a.out, **{"profile_" + p.replace(":", "_"): v for p, v in res["profiles"].items()})
     summary = {"workload": cfg["name"], "wall": a.wall, "spin_T_LET": a.spin, "window_steps": a.window,
-               "stats_every": a.stats_every, "state": res["state"], "errors_vs_f64": res["errors"],
-               "window_s": res["window_s"], "nonfinite": res["nonfinite"],
-               "profile_f64": res["profiles"]["f64"].tolist()}
+               "stats_every": a.stats_every, "state": res["state"], "reference": a.reference,
+               "errors_vs_reference": res["errors"], "window_s": res["window_s"], "nonfinite": res["nonfinite"],
+               "profile_reference": res["profiles"][a.reference].tolist()}
     print(json.dumps(summary))
     return 0
 
