@@ -390,7 +390,12 @@ int lbm_mode_correlation(const int32_t *series, int64_t n, int32_t m_lo, int32_t
  * context holds the state after the T steps.  Needs a context with LBM_HALFWAY wall,
  * LBM_F32 or LBM_F64 precision, no trigger and the default collision model
  * (LBM_EUNSUPPORTED otherwise).  Allocates its temporaries (checkpoints, moments of
- * one segment, two adjoint fields) for the duration of the call (LBM_ENOMEM). */
+ * two segments, two adjoint fields, one per-segment gradient buffer) for the duration of
+ * the call (LBM_ENOMEM).  The reverse sweep recomputes segment s - 1 on a second stream,
+ * created and destroyed by the call and ordered against the context's stream by events,
+ * while the backward steps of segment s run on the context's stream; dJ_dgz is summed per
+ * segment in the storage's compute type and added to FP64 totals after each segment.  The
+ * call synchronises the context's stream before it returns. */
 int lbm_adjoint(lbm_ctx *ctx, int64_t T, int32_t objective, int64_t checkpoint_every,
                 double *J, double *dJ_dgz, double *dJ_domega);
 
