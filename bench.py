@@ -453,9 +453,7 @@ def run_ours(args):
     rho_h = [torch.empty(c, dtype=fdt, pin_memory=True) for c in cells]
     u_h = [torch.empty(3 * c, dtype=fdt, pin_memory=True) for c in cells]
     E_h = None if ensemble else np.empty((cfg["n_sections"], len(cfg["r_over_R"]), cfg["n_modes"] + 1))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    def e2e_step():
         lbm.lbm_set_raw(L.ctx, host_state, nbytes)
         lbm.lbm_step(L.ctx, LBM_STEPS_PER_STEP)
         if not ensemble:
@@ -464,6 +462,13 @@ def run_ours(args):
             L.select(m)
             lbm.lbm_moments(L.ctx, rho_h[m], u_h[m])
         L.select(0)
+
+    for _ in range(2):            # untimed: staging buffers, first touch of the pinned pages
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_val = n_fluid * LBM_STEPS_PER_STEP * max(args.e2e_steps, 1) * world / max(e2e_s, 1e-9) / 1e6
