@@ -520,7 +520,7 @@ def run_ours(args):
         "n_fluid_cells": n_fluid,
         "all_cell_mlups": value * sum(cells) / n_fluid,
         "nonfinite_cells": bad,
-        "launch_shape": info["variant"],
+        "launch_shape": {"even": info["variant"], "odd": info["variant_odd"]},
     }
     line.update(extras)
     print(json.dumps(line), flush=True)
@@ -561,7 +561,7 @@ def measure_precision(lbm, cfg, args, precision, steps, warmup):
     kms, kn = lbm.lbm_profile_read(L.ctx)
     lbm.lbm_profile_enable(L.ctx, False)
     bad = lbm.lbm_reduce(L.ctx)[4]
-    variant = L.info()["variant"]
+    variant = {"even": L.info()["variant"], "odd": L.info()["variant_odd"]}
     L.close()
     peak, _ = measured_peak()
     bpu = BYTES_PER_UPDATE[precision]

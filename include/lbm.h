@@ -150,6 +150,7 @@ typedef struct {
     int32_t step_threads;   /* threads per block of that shape                       */
     int32_t n_variants;     /* launch shapes available for this precision            */
     int32_t graph_chunk;    /* steps per captured graph, 0 = direct launches         */
+    int32_t variant_odd;    /* launch shape of the odd steps (variant: the even ones) */
 } lbm_info;
 
 /* ==== life cycle ====================================================================== */
@@ -273,6 +274,12 @@ int lbm_set_graph(lbm_ctx *ctx, int32_t chunk);
  * collision model is set, or a staged shape the context's walls or rows cannot use). */
 int lbm_set_variant(lbm_ctx *ctx, int32_t variant);
 
+/* Launch shapes per parity of the AA pattern: `even` for the steps with even t (own
+ * slots), `odd` for the others (neighbour slots); lbm_set_variant sets both.  The defaults
+ * are the fastest pair measured on GB300 (F32: 6 even, 9 odd; 16-bit formats: 7 and 9;
+ * Bouzidi walls: 7 and 7; F64: 0 and 0).  Same errors as lbm_set_variant. */
+int lbm_set_variants(lbm_ctx *ctx, int32_t even, int32_t odd);
+
 /* Failure-detection tests of the staged shapes (11, 12): the next step launched directly
  * leaves the copies of staged tile `tile` (0-based, in launch order) unissued, so the CTA
  * waiting for it gives up after its bounded wait (about 2 s, then about 2 s more for its
@@ -283,10 +290,12 @@ int lbm_set_variant(lbm_ctx *ctx, int32_t variant);
  * LBM_EUNSUPPORTED (the current shape is not staged). */
 int lbm_test_expire_wait(lbm_ctx *ctx, int32_t tile);
 
-/* Project autotuner for the launch shape: times `steps` steps (2..10000) of every
- * shape on the context's own problem, restores the populations, t and statistics
- * afterwards, selects the fastest shape and returns it with its time per step
- * (microseconds).  Synchronises; allocates one temporary copy of the populations. */
+/* Project autotuner for the launch shapes: times `steps` steps (2..10000) of every
+ * shape on the context's own problem, the even and the odd steps separately, restores
+ * the populations, t and statistics afterwards, selects the fastest shape for each parity
+ * (lbm_set_variants) and returns the even one in *variant (lbm_get_info reports both) with
+ * the mean time per step of the chosen pair (microseconds).  Synchronises; allocates one
+ * temporary copy of the populations. */
 int lbm_autotune(lbm_ctx *ctx, int32_t steps, int32_t *variant, double *best_us);
 
 /* Every `every` steps (0 = never), lbm_step reduces mass and checks for

@@ -54,7 +54,8 @@ struct lbm_ctx {
     std::vector<int64_t> ev_launches;   // step kernels covered by each timed event pair
     int64_t prof_launches_pending = 0;
     int64_t launches = 0;
-    int variant = 0;                 // launch shape of the step kernel
+    int variant = 0;                 // launch shape of the step kernel at even t
+    int variant_odd = 0;             // ... and at odd t
     int collision = 0;               // collision model of the step kernel (lbm::MODEL_* bits)
     int model_bits = 0;              // lbm_set_collision: MODEL_BGK, MODEL_O2
     std::vector<bool> has_rates;     // per member: a general relaxation matrix was given
@@ -62,7 +63,7 @@ struct lbm_ctx {
     // graph-captured chunks of steps
     int32_t graph_chunk = 0;
     cudaGraphExec_t gexec = nullptr;
-    int gexec_variant = -1, gexec_stats_every = -1;
+    int gexec_variant = -1, gexec_variant_odd = -1, gexec_stats_every = -1;
     lbm::StepTime *d_times = nullptr;        // [graph_chunk] device table read by the graph
     lbm::StepTime *h_times[2] = {nullptr, nullptr};   // pinned staging, double-buffered
     cudaEvent_t h_done[2] = {nullptr, nullptr};
@@ -114,6 +115,7 @@ void lbm::set_thread_error(const char *msg) { g_create_error = msg ? msg : ""; }
 namespace {
 
 using lbm::default_variant;
+using lbm::default_variant_odd;
 using lbm::model_variant;
 
 int set_err(lbm_ctx *c, int code, const char *fmt, ...) {
@@ -401,6 +403,7 @@ int update_collision(lbm_ctx *c) {
     if (code != c->collision) {
         c->collision = code;
         c->variant = code != 0 ? model_variant(c->precision) : default_variant(c->precision, c->wall);
+        c->variant_odd = code != 0 ? model_variant(c->precision) : default_variant_odd(c->precision, c->wall);
         drop_graph(c);
     }
     return LBM_OK;
@@ -476,6 +479,9 @@ int build_member(lbm_ctx *c, const lbm_grid *g, const lbm_relax *r, const lbm_fo
 }
 
 
+// Launch shape of the step with index t.
+int variant_at(const lbm_ctx *c, int64_t t) { return (t & 1) ? c->variant_odd : c->variant; }
+
 StepArgs make_args(const lbm_ctx *c, int64_t t) {
     StepArgs a;
     std::memset(&a, 0, sizeof a);
@@ -489,9 +495,10 @@ StepArgs make_args(const lbm_ctx *c, int64_t t) {
     a.stats = c->stats;
     a.dstride = c->dense_total;
     a.collision = c->collision;
-    const int bs = lbm::step_threads(c->precision, c->variant);
-    const int zc = lbm::step_zc(c->precision, c->variant);
-    const int sk = lbm::staged_of(c->variant);
+    const int v = variant_at(c, t);
+    const int bs = lbm::step_threads(c->precision, v);
+    const int zc = lbm::step_zc(c->precision, v);
+    const int sk = lbm::staged_of(v);
     a.err = c->flags;
     a.skip_tile = -1;
     if (sk >= 0) {
@@ -579,6 +586,7 @@ int create_common(lbm_ctx **out, int32_t n, const lbm_grid *grids, const lbm_rel
     c->precision = prec;
     c->wall = wall;
     c->variant = default_variant(prec, wall);
+    c->variant_odd = lbm::default_variant_odd(prec, wall);
     c->stream = (cudaStream_t)stream;
     c->f16_scale = std::ldexp(1.0f, s16);
     c->f16_inv = std::ldexp(1.0f, -s16);
@@ -687,15 +695,17 @@ bool variant_available(const lbm_ctx *c, int variant) {
 // Configures the kernels of the context's launch shape (shared-memory size of the staged
 // kernels) ahead of any launch or graph capture.
 int prepare_variant(lbm_ctx *c) {
-    if (lbm::staged_of(c->variant) < 0) return LBM_OK;
-    cudaError_t e = cudaSuccess;
-    switch (c->precision) {
-        case LBM_F64: e = lbm::prepare_step<LBM_F64>(c->wall, c->variant); break;
-        case LBM_F32: e = lbm::prepare_step<LBM_F32>(c->wall, c->variant); break;
-        case LBM_F16S: e = lbm::prepare_step<LBM_F16S>(c->wall, c->variant); break;
-        default: e = lbm::prepare_step<LBM_BF16>(c->wall, c->variant); break;
+    for (int v : {c->variant, c->variant_odd}) {
+        if (lbm::staged_of(v) < 0) continue;
+        cudaError_t e = cudaSuccess;
+        switch (c->precision) {
+            case LBM_F64: e = lbm::prepare_step<LBM_F64>(c->wall, v); break;
+            case LBM_F32: e = lbm::prepare_step<LBM_F32>(c->wall, v); break;
+            case LBM_F16S: e = lbm::prepare_step<LBM_F16S>(c->wall, v); break;
+            default: e = lbm::prepare_step<LBM_BF16>(c->wall, v); break;
+        }
+        if (e != cudaSuccess) return cuda_err(c, e, "configuring the staged step kernels");
     }
-    if (e != cudaSuccess) return cuda_err(c, e, "configuring the staged step kernels");
     return LBM_OK;
 }
 
@@ -842,6 +852,7 @@ int lbm_get_info(lbm_ctx *c, lbm_info *info) {
     info->precision = c->precision;
     info->launches = c->launches;
     info->variant = c->variant;
+    info->variant_odd = c->variant_odd;
     info->step_threads = lbm::step_threads(c->precision, c->variant);
     info->n_variants = lbm::step_variants(c->precision);
     info->graph_chunk = c->graph_chunk;
@@ -942,8 +953,8 @@ int lbm_init_fields(lbm_ctx *c, const double *rho, const double *u) {
 
 int lbm_test_expire_wait(lbm_ctx *c, int32_t tile) {
     if (!c) return LBM_EINVAL;
-    if (lbm::staged_of(c->variant) < 0)
-        return set_err(c, LBM_EUNSUPPORTED, "the current launch shape has no staged tiles");
+    if (lbm::staged_of(c->variant) < 0 && lbm::staged_of(c->variant_odd) < 0)
+        return set_err(c, LBM_EUNSUPPORTED, "the current launch shapes have no staged tiles");
     if (tile < 0) return set_err(c, LBM_EINVAL, "tile must be >= 0");
     c->skip_tile = tile;
     return LBM_OK;
@@ -965,7 +976,7 @@ namespace {
 int step_direct(lbm_ctx *c) {
     const bool stats = c->stats && c->stats_every > 0 && (c->t % c->stats_every == 0);
     StepArgs a = make_args(c, c->t);
-    if (c->skip_tile >= 0 && lbm::staged_of(c->variant) >= 0) {
+    if (c->skip_tile >= 0 && lbm::staged_of(variant_at(c, c->t)) >= 0) {
         a.skip_tile = c->skip_tile;
         c->skip_tile = -1;
     }
@@ -976,7 +987,8 @@ int step_direct(lbm_ctx *c) {
         LBM_CUDA(c, cudaEventRecord(e0, c->stream));
     }
     int rc = dispatch(c, [&](auto P) {
-        return lbm::launch_step<decltype(P)::value>(c->wall, (int)(c->t & 1), stats, a, c->variant, c->stream);
+        return lbm::launch_step<decltype(P)::value>(c->wall, (int)(c->t & 1), stats, a, variant_at(c, c->t),
+                                                    c->stream);
     });
     if (rc) return rc;
     if (c->prof) {
@@ -992,6 +1004,7 @@ void drop_graph(lbm_ctx *c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
     c->gexec_variant = -1;
+    c->gexec_variant_odd = -1;
     c->gexec_stats_every = -1;
 }
 
@@ -1010,17 +1023,20 @@ int build_graph(lbm_ctx *c) {
         cudaStreamDestroy(cs);
         return cuda_err(c, e, "cudaStreamBeginCapture");
     }
-    StepArgs a = make_args(c, 0);
-    a.times = c->d_times;
+    // the two parities may run different launch shapes (block counts differ)
+    StepArgs ap[2] = {make_args(c, 0), make_args(c, 1)};
     cudaError_t le = cudaSuccess;
     for (int k = 0; k < c->graph_chunk && le == cudaSuccess; ++k) {
+        StepArgs &a = ap[k & 1];
+        a.times = c->d_times;
         a.tidx = k;
         const bool stats = every > 0 && (k % every == 0);
+        const int v = variant_at(c, k);
         switch (c->precision) {
-            case LBM_F64: le = lbm::launch_step<LBM_F64>(c->wall, k & 1, stats, a, c->variant, cs); break;
-            case LBM_F32: le = lbm::launch_step<LBM_F32>(c->wall, k & 1, stats, a, c->variant, cs); break;
-            case LBM_F16S: le = lbm::launch_step<LBM_F16S>(c->wall, k & 1, stats, a, c->variant, cs); break;
-            default: le = lbm::launch_step<LBM_BF16>(c->wall, k & 1, stats, a, c->variant, cs); break;
+            case LBM_F64: le = lbm::launch_step<LBM_F64>(c->wall, k & 1, stats, a, v, cs); break;
+            case LBM_F32: le = lbm::launch_step<LBM_F32>(c->wall, k & 1, stats, a, v, cs); break;
+            case LBM_F16S: le = lbm::launch_step<LBM_F16S>(c->wall, k & 1, stats, a, v, cs); break;
+            default: le = lbm::launch_step<LBM_BF16>(c->wall, k & 1, stats, a, v, cs); break;
         }
     }
     cudaGraph_t g = nullptr;
@@ -1038,6 +1054,7 @@ int build_graph(lbm_ctx *c) {
         return cuda_err(c, e, "cudaGraphInstantiate");
     }
     c->gexec_variant = c->variant;
+    c->gexec_variant_odd = c->variant_odd;
     c->gexec_stats_every = every;
     return LBM_OK;
 }
@@ -1045,7 +1062,8 @@ int build_graph(lbm_ctx *c) {
 // One replay of the captured chunk starting at the current (aligned) t.
 int step_graph_chunk(lbm_ctx *c) {
     const int every = (c->stats && c->stats_every > 0) ? c->stats_every : 0;
-    if (!c->gexec || c->gexec_variant != c->variant || c->gexec_stats_every != every) {
+    if (!c->gexec || c->gexec_variant != c->variant || c->gexec_variant_odd != c->variant_odd ||
+        c->gexec_stats_every != every) {
         int rc = build_graph(c);
         if (rc) return rc;
     }
@@ -1135,23 +1153,32 @@ int lbm_set_graph(lbm_ctx *c, int32_t chunk) {
     return LBM_OK;
 }
 
-int lbm_set_variant(lbm_ctx *c, int32_t variant) {
+int lbm_set_variants(lbm_ctx *c, int32_t even, int32_t odd) {
     if (!c) return LBM_EINVAL;
-    if (!lbm::step_variant_ok(c->precision, variant))
-        return set_err(c, LBM_EINVAL, "launch-shape variant %d is not available for this storage (0..%d)", variant,
-                       lbm::step_variants(c->precision) - 1);
-    if (c->collision != 0 && variant != model_variant(c->precision))
-        return set_err(c, LBM_EUNSUPPORTED, "the ablation collision models run in the default launch shape only");
-    if (!variant_available(c, variant))
-        return set_err(c, LBM_EUNSUPPORTED,
-                       "launch shape %d (staged) needs pipes with half-way or Bouzidi walls whose rows fit %d "
-                       "elements per segment", variant, lbm::staged_cap(c->precision, std::max(0, lbm::staged_of(variant))));
-    const int old = c->variant;
-    c->variant = variant;
+    for (int variant : {even, odd}) {
+        if (!lbm::step_variant_ok(c->precision, variant))
+            return set_err(c, LBM_EINVAL, "launch-shape variant %d is not available for this storage (0..%d)", variant,
+                           lbm::step_variants(c->precision) - 1);
+        if (c->collision != 0 && variant != model_variant(c->precision))
+            return set_err(c, LBM_EUNSUPPORTED, "the ablation collision models run in the default launch shape only");
+        if (!variant_available(c, variant))
+            return set_err(c, LBM_EUNSUPPORTED,
+                           "launch shape %d (staged) needs pipes with half-way or Bouzidi walls whose rows fit %d "
+                           "elements per segment",
+                           variant, lbm::staged_cap(c->precision, std::max(0, lbm::staged_of(variant))));
+    }
+    const int old_even = c->variant, old_odd = c->variant_odd;
+    c->variant = even;
+    c->variant_odd = odd;
     const int rc = prepare_variant(c);
-    if (rc) c->variant = old;
+    if (rc) {
+        c->variant = old_even;
+        c->variant_odd = old_odd;
+    }
     return rc;
 }
+
+int lbm_set_variant(lbm_ctx *c, int32_t variant) { return lbm_set_variants(c, variant, variant); }
 
 int lbm_set_collision(lbm_ctx *c, int32_t model, int32_t equilibrium) {
     if (!c) return LBM_EINVAL;
@@ -1188,32 +1215,47 @@ int lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *variant, double *best_us) {
     c->stats = nullptr;          // no statistics, checks or profiling while tuning
     c->check_every = 0;
     c->prof = false;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    int best = 0, rc = LBM_OK;
-    double best_t = 1e300;
+    // one event before every timed step and one after the last: the even and the odd steps
+    // are timed separately, so each parity gets its own fastest shape
+    std::vector<cudaEvent_t> ev((size_t)steps + 1, nullptr);
+    int rc = LBM_OK;
+    for (size_t k = 0; k < ev.size() && rc == LBM_OK; ++k)
+        if (cudaEventCreate(&ev[k]) != cudaSuccess) rc = cuda_err(c, cudaGetLastError(), "autotune events");
+    int best[2] = {c->variant, c->variant_odd};
+    double best_t[2] = {1e300, 1e300};
     for (int v = 0; v < nv && rc == LBM_OK; ++v) {
         if (!variant_available(c, v)) continue;
-        c->variant = v;
+        c->variant = c->variant_odd = v;
         rc = prepare_variant(c);
         if (rc) break;
         c->t = t_save;
         for (int k = 0; k < 2 && rc == LBM_OK; ++k) rc = step_direct(c);
         if (rc) break;
-        cudaEventRecord(e0, c->stream);
-        for (int k = 0; k < steps && rc == LBM_OK; ++k) rc = step_direct(c);
-        cudaEventRecord(e1, c->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = cuda_err(c, cudaGetLastError(), "autotune"); break; }
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const double us = 1e3 * ms / steps;
-        if (us < best_t) { best_t = us; best = v; }
+        const int64_t t0 = c->t;
+        for (int k = 0; k < steps && rc == LBM_OK; ++k) {
+            cudaEventRecord(ev[k], c->stream);
+            rc = step_direct(c);
+        }
+        cudaEventRecord(ev[steps], c->stream);
+        if (cudaEventSynchronize(ev[steps]) != cudaSuccess) { rc = cuda_err(c, cudaGetLastError(), "autotune"); break; }
+        double sum[2] = {0, 0};
+        int cnt[2] = {0, 0};
+        for (int k = 0; k < steps; ++k) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            const int par = (int)((t0 + k) & 1);
+            sum[par] += 1e3 * ms;
+            cnt[par] += 1;
+        }
+        for (int par = 0; par < 2; ++par) {
+            const double us = cnt[par] ? sum[par] / cnt[par] : 1e300;
+            if (us < best_t[par]) { best_t[par] = us; best[par] = v; }
+        }
         cudaMemcpyAsync(c->pops, save, bytes, cudaMemcpyDeviceToDevice, c->stream);
     }
     cudaStreamSynchronize(c->stream);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
     dev_free(c, save);
     c->t = t_save;
     c->stats = stats_save;
@@ -1221,10 +1263,14 @@ int lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *variant, double *best_us) {
     c->check_every = check_save;
     c->prof = prof_save;
     c->launches = launches_save;
-    c->variant = best;
+    c->variant = best[0];
+    c->variant_odd = best[1];
+    if (rc == LBM_OK) rc = prepare_variant(c);
+    const int best_v = best[0];
+    const double best_us_pair = 0.5 * (best_t[0] + best_t[1]);
     if (rc) return rc;
-    if (variant) *variant = best;
-    if (best_us) *best_us = best_t;
+    if (variant) *variant = best_v;
+    if (best_us) *best_us = best_us_pair;
     return LBM_OK;
 }
 
@@ -1470,7 +1516,7 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     // or checks; they are restored afterwards
     double *stats_save = c->stats;
     const int64_t check_save = c->check_every;
-    const int variant_save = c->variant;
+    const int variant_save = c->variant, variant_odd_save = c->variant_odd;
     const int32_t chunk_save = c->graph_chunk;
     c->stats = nullptr;
     c->check_every = 0;
@@ -1487,7 +1533,7 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
             if (e != cudaSuccess) { rc = cuda_err(c, e, "checkpoint copy"); break; }
             for (int64_t k = 0; k < ns && rc == LBM_OK; ++k) rc = step_direct(c);
         } else {
-            c->variant = lbm::moments_variant(c->precision);
+            c->variant = c->variant_odd = lbm::moments_variant(c->precision);
             for (int64_t k = 0; k < ns && rc == LBM_OK; ++k) {
                 StepArgs a = make_args(c, c->t);
                 a.moments = (char *)mom + (size_t)(sgm & 1) * mom_seg + (size_t)k * 9 * n * es;
@@ -1607,6 +1653,7 @@ int lbm_adjoint(lbm_ctx *c, int64_t T, int32_t objective, int64_t checkpoint_eve
     c->stats = stats_save;
     c->check_every = check_save;
     c->variant = variant_save;
+    c->variant_odd = variant_odd_save;
     c->graph_chunk = chunk_save;
     cudaStreamSynchronize(c->stream);
     release();

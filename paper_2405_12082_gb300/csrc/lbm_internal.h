@@ -56,6 +56,14 @@ inline int default_variant(int precision, int wall) {
     if (wall == LBM_BOUZIDI) return 7;
     return precision == LBM_F32 ? 6 : 7;
 }
+// the fastest shape of the odd (neighbour-slot) steps: 128 x 7 with 2 planes per thread
+// (more registers for the 27 neighbour addresses and wall-link selects; R = 96 pipe: odd
+// step 0.855 of measured HBM against 0.824 with the even steps' shape)
+inline int default_variant_odd(int precision, int wall) {
+    if (precision == LBM_F64) return 0;
+    if (wall == LBM_BOUZIDI) return 7;
+    return 9;
+}
 // the shape the ablation collision models are compiled for (one plane per thread)
 inline int model_variant(int precision) { return precision == LBM_F64 ? 0 : 2; }
 // the shape of the adjoint's moment-storing recompute (256 x 4, one plane per thread:

@@ -82,7 +82,8 @@ class lbm_info(ctypes.Structure):
     _fields_ = [("n_cells", ctypes.c_int64), ("n_fluid", ctypes.c_int64), ("t", ctypes.c_int64),
                 ("population_bytes", ctypes.c_int64), ("n_members", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("launches", ctypes.c_int64), ("variant", ctypes.c_int32),
-                ("step_threads", ctypes.c_int32), ("n_variants", ctypes.c_int32), ("graph_chunk", ctypes.c_int32)]
+                ("step_threads", ctypes.c_int32), ("n_variants", ctypes.c_int32), ("graph_chunk", ctypes.c_int32),
+                ("variant_odd", ctypes.c_int32)]
 
 
 # device-memory hooks (lbm_set_allocator)
@@ -133,6 +134,7 @@ def _load():
         "lbm_mode_correlation": [P, I64, I32, I32, I32, P],
         "lbm_load": [P, ctypes.c_char_p],
         "lbm_set_variant": [P, I32],
+        "lbm_set_variants": [P, I32, I32],
         "lbm_test_expire_wait": [P, I32],
         "lbm_autotune": [P, I32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
     }
@@ -156,7 +158,7 @@ EXPORTED = ("lbm_create", "lbm_ensemble_create", "lbm_free", "lbm_last_error", "
             "lbm_stats_get", "lbm_modes", "lbm_adjoint", "lbm_profile_enable", "lbm_profile_read",
             "lbm_fluid_mask", "lbm_reduce_static", "lbm_set_graph", "lbm_set_variant", "lbm_autotune",
             "lbm_save", "lbm_load", "lbm_stats_profile", "lbm_dominant_modes", "lbm_transition_matrix",
-            "lbm_mode_correlation", "lbm_set_collision", "lbm_set_allocator", "lbm_test_expire_wait")
+            "lbm_mode_correlation", "lbm_set_collision", "lbm_set_allocator", "lbm_test_expire_wait", "lbm_set_variants")
 
 
 # ---- marshalling helpers -----------------------------------------------------------------
@@ -412,6 +414,10 @@ def lbm_set_graph(ctx, chunk):
 
 def lbm_set_variant(ctx, variant):
     return _check(ctx, LIB.lbm_set_variant(ctx, int(variant)))
+
+
+def lbm_set_variants(ctx, even, odd):
+    return _check(ctx, LIB.lbm_set_variants(ctx, int(even), int(odd)))
 
 
 def lbm_test_expire_wait(ctx, tile):

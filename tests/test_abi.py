@@ -63,7 +63,7 @@ def test_struct_layouts_match_the_header(lbm_lib):
     assert ctypes.sizeof(lbm.lbm_relax) == 16
     assert ctypes.sizeof(lbm.lbm_force) == 264
     assert ctypes.sizeof(lbm.lbm_modes_cfg) == 144
-    assert ctypes.sizeof(lbm.lbm_info) == 64
+    assert ctypes.sizeof(lbm.lbm_info) == 72
 
 
 def test_struct_layouts_match_a_c_compiler(lbm_lib, tmp_path):
@@ -79,7 +79,8 @@ def test_struct_layouts_match_a_c_compiler(lbm_lib, tmp_path):
         "lbm_relax": ["omega", "rates"],
         "lbm_force": ["g", "trigger", "n_modes", "k_theta", "weight", "phase", "A0", "h", "kz", "t_end", "gz_field"],
         "lbm_modes_cfg": ["n_sections", "r_over_R", "n_theta", "n_modes"],
-        "lbm_info": ["n_cells", "population_bytes", "n_members", "precision", "launches", "variant", "graph_chunk"],
+        "lbm_info": ["n_cells", "population_bytes", "n_members", "precision", "launches", "variant", "graph_chunk",
+                     "variant_odd"],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm.h"', "int main(void){"]
     for st, fields in checks.items():

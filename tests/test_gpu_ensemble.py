@@ -156,7 +156,7 @@ def test_autotune_leaves_the_state_untouched(lbm_lib):
     v, us = lbm.lbm_autotune(L.ctx, 6)
     assert 0 <= v < 13 and us > 0
     info = L.info()
-    assert info["t"] == 5 and info["variant"] == v
+    assert info["t"] == 5 and info["variant"] == v and 0 <= info["variant_odd"] < 13
     assert np.array_equal(_populations(lbm, L.ctx, grid), before)
     acc1 = np.empty_like(acc0)
     assert lbm.lbm_stats_get(L.ctx, acc1) == c0
@@ -191,3 +191,35 @@ def test_two_members_match_the_oracle_fp64(lbm_lib):
         assert rel_err(E.populations(), ref.f, ref.fluid) < 1e-12
         L.close()
     E.close()
+
+
+@pytest.mark.parametrize("graph", [0, 4])
+def test_per_parity_shapes_are_bit_identical(lbm_lib, graph):
+    """Different launch shapes for the even and the odd steps (lbm_set_variants), direct and
+    in captured graphs (whose two parities then have different block counts), with
+    statistics on: the same populations and sums as one shape for both."""
+    lbm = lbm_lib
+    grid, relax, force = _member_setup(lbm, MEMBERS[1])
+    out = []
+    for even, odd in ((6, 6), (6, 9), (2, 11), (12, 7), (9, 0)):
+        L = lbm.Lattice(grid, relax, force)
+        lbm.lbm_set_variants(L.ctx, even, odd)
+        info = L.info()
+        assert (info["variant"], info["variant_odd"]) == (even, odd)
+        lbm.lbm_init(L.ctx, "laminar", noise_amp=1e-3, seed=9)
+        lbm.lbm_stats_enable(L.ctx, 2)
+        if graph:
+            lbm.lbm_set_graph(L.ctx, graph)
+        L.step(11)
+        acc = np.empty((4, grid.nz, grid.ny, grid.nx))
+        lbm.lbm_stats_get(L.ctx, acc)
+        out.append((_populations(lbm, L.ctx, grid), acc))
+        L.close()
+    for f, acc in out[1:]:
+        assert np.array_equal(f, out[0][0])
+        assert np.array_equal(acc, out[0][1])
+    L = lbm.Lattice(grid, relax, force)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_set_variants(L.ctx, 6, 99)
+    assert (L.info()["variant"], L.info()["variant_odd"]) == (6, 9)      # unchanged defaults (F32)
+    L.close()

@@ -52,7 +52,8 @@ def _sample(cfg, n, seed):
 @pytest.fixture(scope="module")
 def c2_state(lbm_lib):
     cfg, L, tr = _c2(lbm_lib)
-    assert L.info()["variant"] == 6           # the launch shape the bench times (128 x 8, 2 planes per thread)
+    # the launch shapes the bench times: 128 x 8 (even steps) and 128 x 7 (odd steps), 2 planes per thread
+    assert (L.info()["variant"], L.info()["variant_odd"]) == (6, 9)
     L.init("loglaw", noise_amp=cfg["noise"], seed=Wk.SEED)
     f0 = L.populations()
     L.step(1)
