@@ -499,6 +499,7 @@ def run_ours(args):
         extras["adjoint"] = measure_adjoint(lbm, min(reps, 3))
 
     peak, peak_kind = measured_peak()
+    extras["alu_probe"] = alu_probe(lbm, torch, peak)
     avg_kernel_s = (kernel_ms / kernel_launches) * 1e-3 if kernel_launches else None
     bpu = BYTES_PER_UPDATE[args.precision]
     achieved = bpu * n_fluid / avg_kernel_s / 1e9 if avg_kernel_s else None
@@ -530,6 +531,21 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def alu_probe(lbm, torch, hbm_gbs):
+    """The instruction side of the roofline: the measured FP32 FMA rates of this GPU and, at
+    that issue rate, how many thread instructions one fluid-cell update may take for the step
+    to run at the measured copy bandwidth with each storage (216 B and 108 B per update)."""
+    try:
+        r = lbm.lbm_probe_fp32(torch.cuda.current_stream().cuda_stream)
+    except lbm.LbmError as e:
+        return {"error": str(e)}
+    smsp = 4 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    thread_inst_per_s = r["warp_ffma_per_s_per_smsp"] * smsp * 32
+    r["thread_inst_slots_per_update_at_hbm_roof"] = {
+        prec: thread_inst_per_s / (hbm_gbs * 1e9 / b) for prec, b in (("f32", 216), ("f16s", 108), ("bf16", 108))}
+    return r
 
 
 def measure_precision(lbm, cfg, args, precision, steps, warmup):

@@ -453,6 +453,21 @@ int lbm_fluid_mask(lbm_ctx *ctx, uint8_t *mask);
 int lbm_reduce_static(const void *pops, int32_t precision, int32_t f16_log2_scale, int64_t n_cells,
                       double *out, void *stream);
 
+/* Measured FP32 arithmetic rate of the current device: the instruction-issue side of the
+ * step's roofline (the DRAM side is the measured copy bandwidth).  Not an operation of the
+ * method: a probe, used by bench.py.  Runs kernels of independent fused multiply-adds on
+ * every SM (8 blocks of 256 threads per SM, 8 dependency chains per thread), first as
+ * scalar FFMA, then as paired FFMA2 (two FMAs per instruction), each the best of three
+ * timed launches (CUDA events on `stream`, a cudaStream_t, NULL = default stream) after
+ * one untimed launch, about 30-60 ms in all.  The kernels write no memory.
+ * out: HOST memory for 4 doubles: [0] scalar FP32 rate in TFLOP/s (2 flops per FMA),
+ *      [1] paired rate in TFLOP/s, [2] scalar FFMA warp instructions per second per SM
+ *      sub-partition (the issue rate: divide by the SM clock for instructions per
+ *      cycle), [3] the scalar launch's milliseconds.
+ * Synchronises `stream`; allocates nothing.  Errors: LBM_EINVAL (out NULL), LBM_ECUDA (no
+ * device, event or launch failure); the reason is reported by lbm_last_error(NULL). */
+int lbm_probe_fp32(double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

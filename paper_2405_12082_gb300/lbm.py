@@ -126,6 +126,7 @@ def _load():
         "lbm_profile_read": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
         "lbm_fluid_mask": [P, P],
         "lbm_reduce_static": [P, I32, I32, I64, P, P],
+        "lbm_probe_fp32": [P, P],
         "lbm_set_graph": [P, I32],
         "lbm_save": [P, ctypes.c_char_p],
         "lbm_stats_profile": [P, I32, D, P],
@@ -158,7 +159,8 @@ EXPORTED = ("lbm_create", "lbm_ensemble_create", "lbm_free", "lbm_last_error", "
             "lbm_stats_get", "lbm_modes", "lbm_adjoint", "lbm_profile_enable", "lbm_profile_read",
             "lbm_fluid_mask", "lbm_reduce_static", "lbm_set_graph", "lbm_set_variant", "lbm_autotune",
             "lbm_save", "lbm_load", "lbm_stats_profile", "lbm_dominant_modes", "lbm_transition_matrix",
-            "lbm_mode_correlation", "lbm_set_collision", "lbm_set_allocator", "lbm_test_expire_wait", "lbm_set_variants")
+            "lbm_mode_correlation", "lbm_set_collision", "lbm_set_allocator", "lbm_test_expire_wait", "lbm_set_variants",
+            "lbm_probe_fp32")
 
 
 # ---- marshalling helpers -----------------------------------------------------------------
@@ -442,6 +444,16 @@ def lbm_reduce_static(pops, precision, f16_log2_scale, n_cells, out, stream=None
     if rc != LBM_OK:
         raise LbmError(rc, "lbm_reduce_static: " + LIB.lbm_last_error(None).decode())
     return rc
+
+
+def lbm_probe_fp32(stream=None):
+    """Measured FP32 rate of the current device (see include/lbm.h): a dict with the scalar
+    and paired FMA rates in TFLOP/s and the FFMA warp-instruction rate per SM sub-partition."""
+    out = (ctypes.c_double * 4)()
+    rc = LIB.lbm_probe_fp32(ptr(out), ptr(stream))
+    if rc != LBM_OK:
+        raise LbmError(rc, "lbm_probe_fp32: " + LIB.lbm_last_error(None).decode())
+    return {"ffma_tflops": out[0], "ffma2_tflops": out[1], "warp_ffma_per_s_per_smsp": out[2], "ms": out[3]}
 
 
 class Lattice:

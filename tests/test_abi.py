@@ -119,3 +119,9 @@ def test_allocator_hooks_need_both_or_neither(lbm_lib):
     assert rc == lbm.LBM_EINVAL
     assert "both" in lbm.lbm_last_error(None)
     lbm.lbm_set_allocator()           # both NULL: the default, accepted without a GPU
+
+
+def test_fp32_probe_rejects_a_null_output_on_the_host(lbm_lib):
+    lbm = lbm_lib
+    assert lbm.LIB.lbm_probe_fp32(None, None) == lbm.LBM_EINVAL
+    assert "out" in lbm.lbm_last_error(None)
