@@ -70,7 +70,9 @@ def config_json(cfg, args, n_gpus, graph=0, tuned=None):
            "lbm_steps_per_step": LBM_STEPS_PER_STEP, "l2": "inputs larger than L2 (no flush)",
            "parallelism": "replicas x%d" % n_gpus, "graph_chunk": graph}
     if tuned is not None:
-        out["launch_shape"] = {"variant": tuned[0], "us_per_step": tuned[1]}
+        # the shapes themselves are the line's launch_shape key (even and odd steps)
+        out["launch_shape"] = {"chosen_by": "--variant" if tuned[1] is None else "lbm_autotune",
+                               "mean_us_per_step": tuned[1]}
     if args.workload == "c4":
         mem = Wk.ensemble_members(Wk.SEED, cfg["n"], cfg["radii"], cfg["u_star"])
         out.update({"members": cfg["n"], "radii": [m["R"] for m in mem], "nz": cfg["nz"],
@@ -404,6 +406,8 @@ def run_ours(args):
         tuned = (args.variant, None)
     elif args.autotune or ensemble:
         tuned = lbm.lbm_autotune(L.ctx, 20)
+    shapes = L.info()             # the launch shapes the timed steps run (after any tuning)
+    shapes = {"even": shapes["variant"], "odd": shapes["variant_odd"]}
     graph = args.graph if args.graph is not None else (LBM_STEPS_PER_STEP if ensemble else 0)
     if graph:
         lbm.lbm_set_graph(L.ctx, graph)
@@ -524,7 +528,7 @@ def run_ours(args):
         "n_fluid_cells": n_fluid,
         "all_cell_mlups": value * sum(cells) / n_fluid,
         "nonfinite_cells": bad,
-        "launch_shape": {"even": info["variant"], "odd": info["variant_odd"]},
+        "launch_shape": shapes,
     }
     line.update(extras)
     print(json.dumps(line), flush=True)
